@@ -1,0 +1,151 @@
+/*
+ * powersort.h -- C ABI of the GB300 (sm_103a) powersort library, libpowersort.so.
+ *
+ * The library sorts keys (with an optional 32-bit payload) stably and in place, as natural
+ * mergesort in the merge order of powersort: J. I. Munro and S. Wild, "Nearly-Optimal
+ * Mergesorts: Fast, Practical Sorting Methods That Optimally Adapt to Existing Runs",
+ * arXiv 1805.04154 (the problem statement is a stable sort, Sec. 1; the method is Alg. 2).
+ * All sorting work runs in the library's own CUDA kernels on one GPU:
+ *   1. run detection  -- maximal weakly ascending / strictly descending runs (Sec. 2),
+ *   2. node powers    -- Definition "Node Power", one integer computation per run boundary,
+ *   3. merge tree     -- the Cartesian tree of the powers (Corollary "Cartesian tree"),
+ *   4. merges         -- the tree's stable merges, scheduled level by level.
+ * The result equals the stable sort of the (key, payload) pairs, bit for bit, including the
+ * order of equal keys.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* or documented as "device" are CUDA device pointers owned by the caller;
+ *     the library never frees caller memory.  "host" pointers are ordinary host memory.
+ *   - keys and vals must be 16-byte aligned (cudaMalloc / PyTorch allocations are).  Bulk copies
+ *     may read, but never write, up to 15 bytes past the end of either array inside its last
+ *     16-byte block.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Sorting calls
+ *     are stream-ordered: they return once all work is enqueued; argument errors are returned
+ *     synchronously.  Each sort synchronizes the stream once, after planning, to size its
+ *     launches.  Errors posted later by the device are reported by ps_stream_status.
+ *   - Limits: one call sorts fewer than 2^31 elements in total (PS_ERR_UNSUPPORTED otherwise).
+ *   - Thread safety: calls on different streams may run concurrently; a workspace must not be
+ *     shared by calls in flight at the same time.
+ */
+#ifndef POWERSORT_H_
+#define POWERSORT_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ps_status {
+  PS_OK = 0,
+  PS_ERR_INVALID_ARG = 1,    /* bad pointer, size, key type, alignment or segment offsets */
+  PS_ERR_UNSUPPORTED = 2,    /* n >= 2^31 */
+  PS_ERR_OUT_OF_MEMORY = 3,  /* workspace allocation failed or workspace too small */
+  PS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
+  PS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up (results are not valid) */
+  PS_ERR_INTERNAL = 6        /* an internal consistency check failed */
+} ps_status;
+
+typedef enum ps_key_type {
+  PS_KEY_I32 = 0, /* int32, signed order */
+  PS_KEY_U32 = 1, /* uint32 */
+  PS_KEY_U64 = 2, /* uint64 */
+  PS_KEY_F32 = 3  /* binary32 in IEEE 754 totalOrder: -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN;
+                     the keys are moved as bit patterns and never altered */
+} ps_key_type;
+
+/* Statistics of the powersort plan of an array (Sec. 2.3 merge cost; Sec. 2 entropy). */
+typedef struct ps_stats {
+  int64_t n;             /* elements */
+  int64_t runs;          /* r, detected runs (all segments) */
+  uint64_t merge_cost;   /* M = sum over runs of (leaf depth x run length) */
+  double entropy_bits;   /* H(L_1/n, ..., L_r/n) of a single array (float accumulation) */
+  int32_t max_depth;     /* deepest leaf of the merge tree */
+  int32_t merge_passes;  /* level passes over HBM */
+  int64_t small_tasks;   /* subtrees merged entirely in shared memory */
+} ps_stats;
+
+/* Bytes of device workspace the *_ws entry points need for n elements (segmented != 0 for the
+ * segmented entry points).  Depends only on the arguments. */
+size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented);
+
+/* Stable in-place sort of keys[0..n) (device, key_type elements) carrying vals[0..n) (device
+ * uint32 payload, or NULL), powersort merge order (Alg. 2).  workspace: device memory of at least
+ * ps_workspace_size(key_type, vals != NULL, n, 0) bytes, 256-byte aligned, caller-owned.
+ * n = 0 or 1 is a no-op.  Errors: PS_ERR_INVALID_ARG (null/misaligned pointers, n < 0, unknown
+ * key type), PS_ERR_OUT_OF_MEMORY (workspace too small), PS_ERR_UNSUPPORTED (n >= 2^31),
+ * PS_ERR_CUDA, PS_ERR_TIMEOUT. */
+ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,
+                     size_t workspace_bytes, void* stream);
+
+/* As ps_sort_ws, with the workspace taken from a library-owned, stream-ordered device memory pool
+ * (allocated and released on `stream`; the pool keeps freed memory for reuse). */
+ps_status ps_sort(int key_type, void* keys, uint32_t* vals, int64_t n, void* stream);
+
+/* Typed conveniences: ps_sort with the key type fixed. */
+ps_status ps_sort_i32(int32_t* keys, uint32_t* vals, int64_t n, void* stream);
+ps_status ps_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, void* stream);
+ps_status ps_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, void* stream);
+ps_status ps_sort_f32(float* keys, uint32_t* vals, int64_t n, void* stream);
+
+/* Segmented sort: every segment [offsets[k], offsets[k+1]) of keys/vals is sorted on its own by
+ * powersort (segment-relative positions in the node powers), all segments in the same launches.
+ * d_offsets: device int64[count+1], offsets[0] = 0, non-decreasing, offsets[count] = n; empty
+ * segments are allowed.  Offsets that break these rules are detected on the device and
+ * reported as PS_ERR_INVALID_ARG (nothing is moved).  workspace as for ps_sort_ws with
+ * segmented = 1. */
+ps_status ps_sort_segmented_ws(int key_type, void* keys, uint32_t* vals, int64_t n,
+                               const int64_t* d_offsets, int64_t count, void* workspace,
+                               size_t workspace_bytes, void* stream);
+
+/* As ps_sort_segmented_ws; n is read from d_offsets[count] (one small device-to-host copy) and
+ * the workspace comes from the library's pool. */
+ps_status ps_sort_segmented(int key_type, void* keys, uint32_t* vals, const int64_t* d_offsets,
+                            int64_t count, void* stream);
+
+/* Merge cost M of powersort's merge tree for runs of the given lengths (host int64[r], each
+ * > 0, sum < 2^62): M = sum_i d_i L_i with d_i the depth of run i in the Cartesian tree of the
+ * node powers (Sec. 2.3, Definition "Node Power", Corollary "Cartesian tree").  Host-only
+ * computation.  Errors: PS_ERR_INVALID_ARG for null pointers, r <= 0, a length <= 0 or overflow. */
+ps_status ps_merge_cost(const int64_t* run_lengths, int64_t r, uint64_t* out_cost);
+
+/* Stages 1-3 on the device without moving any element: run detection, node powers, merge tree.
+ * keys: device array (not modified); d_offsets/count as for ps_sort_segmented_ws, or NULL / 1
+ * for one array; workspace as for ps_sort_ws (segmented = d_offsets != NULL).  Host outputs,
+ * each optional (NULL to skip), capacity n + 1 entries; r = *out_runs:
+ *   starts[r+1]     run starts (starts[r] = n)
+ *   desc[r]         1 if the run was strictly descending
+ *   power[r+1]      node power of boundary j between runs j-1 and j (0 at j = 0, j = r and at
+ *                   segment boundaries)
+ *   leaf_depth[r]   depth of run i in the merge tree
+ *   node_left[r+1], node_right[r+1]  for boundary j with power >= 1, its merge joins runs
+ *                   [node_left[j], j) and [j, node_right[j]) (undefined elsewhere)
+ *   node_depth[r+1] depth of boundary j's node (undefined where power is 0)
+ * *out_cost receives M.  Synchronizes the stream. */
+ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d_offsets,
+                     int64_t count, void* workspace, size_t workspace_bytes, int64_t* out_runs,
+                     uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power,
+                     uint8_t* leaf_depth, int32_t* node_left, int32_t* node_right,
+                     uint8_t* node_depth, void* stream);
+
+/* Plan statistics of one array (keys on the device, not modified; workspace from the pool).
+ * Synchronizes the stream. */
+ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream);
+
+/* Synchronizes `stream`, then reports (and clears) errors the device posted on the current
+ * device since the last call: PS_ERR_TIMEOUT if a bounded wait gave up, PS_ERR_CUDA if the
+ * stream itself failed, else PS_OK. */
+ps_status ps_stream_status(void* stream);
+
+/* Static description of a status code (never NULL). */
+const char* ps_status_string(ps_status status);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int ps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* POWERSORT_H_ */

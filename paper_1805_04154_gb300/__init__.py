@@ -1,0 +1,235 @@
+"""GB300 powersort: stable natural mergesort in powersort's merge order (Munro & Wild,
+arXiv 1805.04154), as hand-written CUDA kernels for sm_103a behind a C ABI.
+
+This module is the thin Python binding of ``libpowersort.so`` (``include/powersort.h``): it
+marshals PyTorch CUDA tensors (pointers, sizes, the current stream, a workspace tensor from
+PyTorch's caching allocator) into the C entry points of the same names.  Every step of the sort
+runs in the library's kernels; there is no CPU or PyTorch fallback, and importing this module
+fails loudly when the library has not been built (``__graft_entry__.build()``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+import torch
+
+__all__ = [
+    "PowersortError", "PS_KEY_I32", "PS_KEY_U32", "PS_KEY_U64", "PS_KEY_F32", "lib_path", "load",
+    "ps_sort", "ps_sort_ws", "ps_sort_segmented", "ps_sort_segmented_ws", "ps_workspace_size",
+    "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
+    "ps_version", "key_type_of",
+]
+
+PS_KEY_I32, PS_KEY_U32, PS_KEY_U64, PS_KEY_F32 = 0, 1, 2, 3
+_STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_OUT_OF_MEMORY",
+           4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT", 6: "PS_ERR_INTERNAL"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+lib_path = os.path.join(_HERE, "libpowersort.so")
+_lib = None
+_lock = threading.Lock()
+
+
+class PowersortError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {_STATUS.get(status, status)} ({ps_status_string(status)})")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("runs", ctypes.c_int64), ("merge_cost", ctypes.c_uint64),
+                ("entropy_bits", ctypes.c_double), ("max_depth", ctypes.c_int32),
+                ("merge_passes", ctypes.c_int32), ("small_tasks", ctypes.c_int64)]
+
+
+def load():
+    """Load libpowersort.so (built in-tree); raises if it is missing."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(lib_path):
+                raise ImportError(f"{lib_path} is missing: build it with __graft_entry__.build()")
+            lib = ctypes.CDLL(lib_path)
+            vp, i32, i64, u64, sz = (ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64,
+                                     ctypes.c_size_t)
+            sigs = {
+                "ps_workspace_size": ([i32, i32, i64, i32], sz),
+                "ps_sort_ws": ([i32, vp, vp, i64, vp, sz, vp], i32),
+                "ps_sort": ([i32, vp, vp, i64, vp], i32),
+                "ps_sort_i32": ([vp, vp, i64, vp], i32),
+                "ps_sort_u32": ([vp, vp, i64, vp], i32),
+                "ps_sort_u64": ([vp, vp, i64, vp], i32),
+                "ps_sort_f32": ([vp, vp, i64, vp], i32),
+                "ps_sort_segmented_ws": ([i32, vp, vp, i64, vp, i64, vp, sz, vp], i32),
+                "ps_sort_segmented": ([i32, vp, vp, vp, i64, vp], i32),
+                "ps_merge_cost": ([vp, i64, vp], i32),
+                "ps_analyze": ([i32, vp, i64, vp, i64, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp], i32),
+                "ps_sort_stats": ([i32, vp, i64, vp, vp], i32),
+                "ps_stream_status": ([vp], i32),
+                "ps_status_string": ([i32], ctypes.c_char_p),
+                "ps_version": ([], i32),
+            }
+            for name, (args, res) in sigs.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = lib
+    return _lib
+
+
+def ps_status_string(status: int) -> str:
+    return load().ps_status_string(int(status)).decode()
+
+
+def ps_version() -> int:
+    return int(load().ps_version())
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise PowersortError(status, where)
+
+
+def key_type_of(t: torch.Tensor) -> int:
+    dt = t.dtype
+    if dt == torch.int32:
+        return PS_KEY_I32
+    if dt == torch.float32:
+        return PS_KEY_F32
+    if dt == torch.int64 or dt == getattr(torch, "uint64", None):
+        return PS_KEY_U64
+    if dt == getattr(torch, "uint32", None):
+        return PS_KEY_U32
+    raise TypeError(f"unsupported key dtype {dt}")
+
+
+def _stream_ptr(stream, device) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor | None, name: str):
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def ps_workspace_size(key_type: int, has_vals: bool, n: int, segmented: bool = False) -> int:
+    return int(load().ps_workspace_size(key_type, 1 if has_vals else 0, n, 1 if segmented else 0))
+
+
+def _workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def ps_sort_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
+               key_type: int | None = None, stream=None) -> None:
+    """Stable in-place sort of ``keys`` (and ``vals``) with a caller-provided workspace tensor."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
+        raise ValueError("vals must hold n 32-bit payloads")
+    _check(load().ps_sort_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                             _dev_ptr(workspace, "workspace"), workspace.numel(),
+                             _stream_ptr(stream, keys.device)), "ps_sort_ws")
+
+
+def ps_sort(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: int | None = None,
+            stream=None, pool: bool = False) -> torch.Tensor:
+    """Stable in-place powersort of a CUDA tensor of keys (int32 / uint32 / uint64 / float32 in
+    IEEE totalOrder), carrying an optional 32-bit payload.  The workspace comes from PyTorch's
+    caching allocator, or from the library's own stream-ordered pool when ``pool``."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
+        raise ValueError("vals must hold n 32-bit payloads")
+    sp = _stream_ptr(stream, keys.device)
+    if pool:
+        _check(load().ps_sort(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n, sp), "ps_sort")
+        return keys
+    ws = _workspace(ps_workspace_size(kt, vals is not None, n), keys.device)
+    _check(load().ps_sort_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                             _dev_ptr(ws, "workspace"), ws.numel(), sp), "ps_sort")
+    return keys
+
+
+def ps_sort_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: torch.Tensor,
+                      key_type: int | None = None, stream=None) -> torch.Tensor:
+    """Sort every segment [offsets[k], offsets[k+1]) on its own (offsets: CUDA int64, count+1)."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if offsets.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    count = offsets.numel() - 1
+    ws = _workspace(ps_workspace_size(kt, vals is not None, n, True), keys.device)
+    _check(load().ps_sort_segmented_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                                       _dev_ptr(offsets, "offsets"), count, _dev_ptr(ws, "workspace"),
+                                       ws.numel(), _stream_ptr(stream, keys.device)),
+           "ps_sort_segmented")
+    return keys
+
+
+def ps_sort_segmented_ws(keys, vals, offsets, workspace, key_type=None, stream=None) -> None:
+    kt = key_type_of(keys) if key_type is None else key_type
+    _check(load().ps_sort_segmented_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
+                                       _dev_ptr(offsets, "offsets"), offsets.numel() - 1,
+                                       _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                       _stream_ptr(stream, keys.device)), "ps_sort_segmented_ws")
+
+
+def ps_merge_cost(run_lengths) -> int:
+    """Powersort merge cost M of runs with the given lengths (host computation)."""
+    L = np.ascontiguousarray(run_lengths, dtype=np.int64)
+    out = ctypes.c_uint64(0)
+    _check(load().ps_merge_cost(ctypes.c_void_p(L.ctypes.data), L.size, ctypes.byref(out)),
+           "ps_merge_cost")
+    return int(out.value)
+
+
+def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type: int | None = None,
+               stream=None) -> dict:
+    """Run detection, node powers and merge tree on the device (keys untouched); returns numpy
+    arrays: starts, desc, power, leaf_depth, node_left, node_right, node_depth, and runs, cost."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    seg = offsets is not None
+    ws = _workspace(ps_workspace_size(kt, False, n, seg), keys.device)
+    cap = n + 2
+    out = {"starts": np.zeros(cap, np.int32), "desc": np.zeros(cap, np.uint8), "power": np.zeros(cap, np.uint8),
+           "leaf_depth": np.zeros(cap, np.uint8), "node_left": np.zeros(cap, np.int32),
+           "node_right": np.zeros(cap, np.int32), "node_depth": np.zeros(cap, np.uint8)}
+    runs = ctypes.c_int64(0)
+    cost = ctypes.c_uint64(0)
+    p = {k: ctypes.c_void_p(v.ctypes.data) for k, v in out.items()}
+    _check(load().ps_analyze(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
+                             (offsets.numel() - 1) if seg else 1, _dev_ptr(ws, "workspace"), ws.numel(),
+                             ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"], p["power"],
+                             p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
+                             _stream_ptr(stream, keys.device)), "ps_analyze")
+    r = int(runs.value)
+    res = {"runs": r, "cost": int(cost.value), "starts": out["starts"][: r + 1].copy(),
+           "desc": out["desc"][:r].copy(), "power": out["power"][: r + 1].copy(),
+           "leaf_depth": out["leaf_depth"][:r].copy(), "node_left": out["node_left"][: r + 1].copy(),
+           "node_right": out["node_right"][: r + 1].copy(), "node_depth": out["node_depth"][: r + 1].copy()}
+    return res
+
+
+def ps_sort_stats(keys: torch.Tensor, key_type: int | None = None, stream=None) -> dict:
+    kt = key_type_of(keys) if key_type is None else key_type
+    st = _Stats()
+    _check(load().ps_sort_stats(kt, _dev_ptr(keys, "keys"), keys.numel(), ctypes.byref(st),
+                                _stream_ptr(stream, keys.device)), "ps_sort_stats")
+    return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+
+def ps_stream_status(stream=None, device=None) -> int:
+    """Synchronize the stream and return (and clear) device-posted status (0 = ok)."""
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return int(load().ps_stream_status(ctypes.c_void_p(stream.cuda_stream)))

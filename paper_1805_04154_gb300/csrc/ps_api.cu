@@ -1,0 +1,415 @@
+// C-ABI entry points of libpowersort.so (declared in include/powersort.h): argument checks,
+// workspace layout, and the stage sequence
+//   detect runs -> node powers -> merge tree -> plan -> [one D2H of the plan header]
+//   -> small subtrees in SMEM + large-leaf placement -> level passes, deepest first.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "powersort.h"
+#include "ps_internal.h"
+
+namespace {
+
+using namespace ps;
+
+constexpr int kMaxDevices = 64;
+
+const KeyLaunch* launch_for(int kt) {
+  switch (kt) {
+    case PS_KEY_I32: return &kLaunchI32;
+    case PS_KEY_U32: return &kLaunchU32;
+    case PS_KEY_U64: return &kLaunchU64;
+    case PS_KEY_F32: return &kLaunchF32;
+  }
+  return nullptr;
+}
+
+int key_bytes(int kt) { return kt == PS_KEY_U64 ? 8 : 4; }
+
+// Carve the workspace into the per-call arrays.  With base == nullptr only the size is computed.
+size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented) {
+  size_t cur = 0;
+  auto take = [&](size_t bytes) -> void* {
+    cur = (cur + 255) & ~(size_t)255;
+    void* p = base ? (void*)(base + cur) : nullptr;
+    cur += std::max<size_t>(bytes, 16);
+    return p;
+  };
+  const size_t kb = (size_t)key_bytes(kt);
+  const size_t N = (size_t)n + 2;
+  c.k[1] = take((((size_t)n * kb + 15) & ~(size_t)15) + 16);
+  c.v[1] = vals ? (uint32_t*)take((((size_t)n * 4 + 15) & ~(size_t)15) + 16) : nullptr;
+  c.S = (int32_t*)take(N * 4);
+  c.run_desc = (uint8_t*)take(N);
+  c.run_seg = segmented ? (int32_t*)take(N * 4) : nullptr;
+  c.P = (uint8_t*)take(N);
+  c.nodeL = (int32_t*)take(N * 4);
+  c.nodeR = (int32_t*)take(N * 4);
+  c.ndepth = (uint8_t*)take(N);
+  c.ldepth = (uint8_t*)take(N);
+  c.detect_tiles = (int32_t)((n + kDetectTile - 1) / kDetectTile);
+  c.detect_state = (uint64_t*)take((size_t)std::max<int32_t>(c.detect_tiles, 1) * 8);
+  const size_t tree_tiles = (size_t)(n + 1) / kTreeTile + 1;
+  c.tree_sum = (int32_t*)take(tree_tiles * 32 * 4);
+  c.tree_pre = (int32_t*)take(tree_tiles * 32 * 4);
+  c.sub_lim = sub_tile((int)kb);
+  c.small_tasks = (int32_t*)take(N * 4);
+  const size_t cap = (size_t)n / (size_t)(c.sub_lim + 1) + 2;
+  c.leaf_items = (int32_t*)take(cap * 4);
+  c.leaf_tile_off = (uint32_t*)take(cap * 4);
+  c.level_cap = (int32_t)cap;
+  c.level_items = (int32_t*)take((size_t)kMaxLevels * cap * 4);
+  c.level_tile_off = (uint32_t*)take((size_t)kMaxLevels * cap * 4);
+  c.tiles_cap = (int32_t)((size_t)n / kMergeTile + 2 * cap + 2);
+  c.tiles = (TileDesc*)take((size_t)c.tiles_cap * sizeof(TileDesc));
+  c.hdr = (PlanHeader*)take(sizeof(PlanHeader));
+  c.d_entropy = (double*)take(sizeof(double));
+  return (cur + 255) & ~(size_t)255;
+}
+
+// ---- per-device library state: status word and memory pool --------------------------------
+std::mutex g_mu;
+uint32_t* g_status[kMaxDevices] = {};
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+uint32_t* lib_status_word(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  if (!g_status[dev]) {
+    uint32_t* p = nullptr;
+    if (cudaMalloc(&p, 64) != cudaSuccess) return nullptr;
+    if (cudaMemset(p, 0, 64) != cudaSuccess) return nullptr;
+    g_status[dev] = p;
+  }
+  return g_status[dev];
+}
+
+cudaMemPool_t lib_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    uint64_t keep = ~0ull;  // keep freed blocks for reuse instead of returning them at syncs
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = pool;
+  }
+  return g_pool[dev];
+}
+
+struct AnalyzeOut {
+  int64_t* runs;
+  uint64_t* cost;
+  int32_t* starts;
+  uint8_t* desc;
+  uint8_t* power;
+  uint8_t* leaf_depth;
+  int32_t* node_left;
+  int32_t* node_right;
+  uint8_t* node_depth;
+  ps_stats* stats;
+};
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+ps_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return PS_OK;
+  if (e == cudaErrorMemoryAllocation) return PS_ERR_OUT_OF_MEMORY;
+  return PS_ERR_CUDA;
+}
+
+#define PS_TRY(expr)                                \
+  do {                                              \
+    cudaError_t e_ = (expr);                        \
+    if (e_ != cudaSuccess) return cuda_status(e_);  \
+  } while (0)
+
+ps_status check_args(int kt, const void* keys, const uint32_t* vals, int64_t n) {
+  if (!launch_for(kt)) return PS_ERR_INVALID_ARG;
+  if (n < 0) return PS_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n > 0 && (!keys || !aligned16(keys))) return PS_ERR_INVALID_ARG;
+  if (vals && !aligned16(vals)) return PS_ERR_INVALID_ARG;
+  return PS_OK;
+}
+
+// The whole pipeline.  With `an` set, stops after planning and reports the plan instead.
+ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
+              bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an) {
+  ps_status st = check_args(kt, keys, vals, n);
+  if (st != PS_OK) return st;
+  if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
+  if (n == 0 || (n == 1 && !an)) {
+    if (an) {
+      if (an->runs) *an->runs = 0;
+      if (an->cost) *an->cost = 0;
+      if (an->starts) an->starts[0] = 0;
+      if (an->power) an->power[0] = 0;
+      if (an->stats) {
+        std::memset(an->stats, 0, sizeof(ps_stats));
+      }
+    }
+    return PS_OK;
+  }
+  Ctx c;
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented);
+  if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  c.stream = s;
+  c.kt = kt;
+  c.key_bytes = key_bytes(kt);
+  c.has_vals = vals != nullptr;
+  c.n = (int32_t)n;
+  c.offsets = segmented ? d_offsets : nullptr;
+  c.count = segmented ? (int32_t)count : 1;
+  c.k[0] = keys;
+  c.v[0] = vals;
+  c.lib_status = lib_status_word(dev);
+  const KeyLaunch* kl = launch_for(kt);
+
+  PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
+  PS_TRY(cudaMemsetAsync(c.detect_state, 0, (size_t)c.detect_tiles * 8, s));
+  if (segmented) PS_TRY(launch_check_offsets(c));
+  PS_TRY(kl->detect(c));
+  PS_TRY(launch_meta_stages(c));
+  if (an && an->stats) {
+    PS_TRY(cudaMemsetAsync(c.d_entropy, 0, sizeof(double), s));
+    PS_TRY(launch_entropy(c, c.d_entropy));
+  }
+  PlanHeader h;
+  PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
+  PS_TRY(cudaStreamSynchronize(s));
+  if (h.status & kDevBadOffsets) return PS_ERR_INVALID_ARG;
+  if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
+  if (h.status & kDevInternal) return PS_ERR_INTERNAL;
+  const int32_t r = h.runs;
+  if (r < 1 || r > n) return PS_ERR_INTERNAL;
+
+  if (an) {
+    if (an->runs) *an->runs = r;
+    if (an->cost) *an->cost = h.cost;
+    const size_t R1 = (size_t)r + 1;
+    if (an->starts) PS_TRY(cudaMemcpyAsync(an->starts, c.S, R1 * 4, cudaMemcpyDeviceToHost, s));
+    if (an->desc) PS_TRY(cudaMemcpyAsync(an->desc, c.run_desc, (size_t)r, cudaMemcpyDeviceToHost, s));
+    if (an->power) PS_TRY(cudaMemcpyAsync(an->power, c.P, R1, cudaMemcpyDeviceToHost, s));
+    if (an->leaf_depth) PS_TRY(cudaMemcpyAsync(an->leaf_depth, c.ldepth, (size_t)r, cudaMemcpyDeviceToHost, s));
+    if (an->node_left) PS_TRY(cudaMemcpyAsync(an->node_left, c.nodeL, R1 * 4, cudaMemcpyDeviceToHost, s));
+    if (an->node_right) PS_TRY(cudaMemcpyAsync(an->node_right, c.nodeR, R1 * 4, cudaMemcpyDeviceToHost, s));
+    if (an->node_depth) PS_TRY(cudaMemcpyAsync(an->node_depth, c.ndepth, R1, cudaMemcpyDeviceToHost, s));
+    double ent = 0.0;
+    if (an->stats) PS_TRY(cudaMemcpyAsync(&ent, c.d_entropy, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PS_TRY(cudaStreamSynchronize(s));
+    if (an->stats) {
+      ps_stats* o = an->stats;
+      o->n = n;
+      o->runs = r;
+      o->merge_cost = h.cost;
+      const double dn = (double)n;
+      o->entropy_bits = (dn * std::log2(dn) - ent) / dn;
+      o->max_depth = h.max_leaf_depth;
+      int passes = 0;
+      for (int d = 0; d < kMaxLevels; ++d)
+        if (h.level_ctr[d] & 0xffffffffull) ++passes;
+      o->merge_passes = passes;
+      o->small_tasks = h.n_small;
+    }
+    return PS_OK;
+  }
+
+  PS_TRY(kl->small(c, h.n_small));
+  PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), (uint32_t)(h.leaf_ctr & 0xffffffffull)));
+  for (int d = kMaxLevels - 1; d >= 0; --d) {
+    const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
+    if (tiles == 0) continue;
+    if ((int64_t)tiles > c.tiles_cap || (int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
+    PS_TRY(kl->level(c, d, items, tiles));
+  }
+  return PS_OK;
+}
+
+ps_status with_pool(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
+                    bool segmented, cudaStream_t s, AnalyzeOut* an) {
+  ps_status st = check_args(kt, keys, vals, n);
+  if (st != PS_OK) return st;
+  if (n <= 1 && !an) return PS_OK;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return PS_ERR_CUDA;
+  Ctx tmp;
+  const size_t bytes = carve(tmp, nullptr, kt, vals != nullptr, n, segmented);
+  void* ws = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&ws, bytes, pool, s);
+  if (e != cudaSuccess) return PS_ERR_OUT_OF_MEMORY;
+  st = run(kt, keys, vals, n, d_offsets, count, segmented, ws, bytes, s, an);
+  e = cudaFreeAsync(ws, s);
+  if (st == PS_OK && e != cudaSuccess) st = PS_ERR_CUDA;
+  return st;
+}
+
+// ---- host merge cost (ps_merge_cost) --------------------------------------------------------
+// Node powers from the first 62 fractional bits of the normalised midpoints (exact for
+// n <= 2^62, since then b - a >= 1/n), the Cartesian tree by a stack, depths top-down by power.
+ps_status host_merge_cost(const int64_t* len, int64_t r, uint64_t* out) {
+  std::vector<uint64_t> S((size_t)r + 1, 0);
+  for (int64_t i = 0; i < r; ++i) {
+    if (len[i] <= 0) return PS_ERR_INVALID_ARG;
+    S[i + 1] = S[i] + (uint64_t)len[i];
+    if (S[i + 1] > ((uint64_t)1 << 62)) return PS_ERR_INVALID_ARG;
+  }
+  const unsigned __int128 two_n = (unsigned __int128)(2 * S[r]);
+  std::vector<int> P((size_t)r + 1, 0);
+  for (int64_t j = 1; j < r; ++j) {
+    const unsigned __int128 l2 = (unsigned __int128)(S[j - 1] + S[j]);
+    const unsigned __int128 r2 = (unsigned __int128)(S[j] + S[j + 1]);
+    const uint64_t x = (uint64_t)((l2 << 62) / two_n), y = (uint64_t)((r2 << 62) / two_n);
+    P[j] = __builtin_clzll(x ^ y) - 1;
+  }
+  // parent of every boundary in the min-Cartesian tree (sentinels 0 and r have power 0)
+  std::vector<int64_t> left((size_t)r + 1, 0), right((size_t)r + 1, r), stk;
+  for (int64_t j = 0; j <= r; ++j) {
+    while (!stk.empty() && P[stk.back()] >= P[j]) stk.pop_back();
+    left[j] = stk.empty() ? 0 : stk.back();
+    stk.push_back(j);
+  }
+  stk.clear();
+  for (int64_t j = r; j >= 0; --j) {
+    while (!stk.empty() && P[stk.back()] >= P[j]) stk.pop_back();
+    right[j] = stk.empty() ? r : stk.back();
+    stk.push_back(j);
+  }
+  // depths in increasing power order (a parent's power is smaller than its child's)
+  std::vector<std::vector<int64_t>> by_power(64);
+  for (int64_t j = 1; j < r; ++j) by_power[P[j]].push_back(j);
+  std::vector<int> depth((size_t)r + 1, 0);
+  for (int p = 1; p < 64; ++p)
+    for (int64_t j : by_power[p]) {
+      const int64_t L = left[j], R = right[j];
+      const int pl = P[L], pr = P[R];
+      if (pl == 0 && pr == 0) depth[j] = 0;
+      else depth[j] = depth[pl > pr ? L : R] + 1;
+    }
+  uint64_t cost = 0;
+  for (int64_t i = 0; i < r; ++i) {
+    const int pl = P[i], pr = P[i + 1];
+    const int d = (pl == 0 && pr == 0) ? 0 : depth[pl > pr ? i : i + 1] + 1;
+    cost += (uint64_t)d * (uint64_t)len[i];
+  }
+  *out = cost;
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented) {
+  if (!launch_for(key_type) || n < 0) return 0;
+  Ctx c;
+  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0);
+}
+
+ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,
+                     size_t workspace_bytes, void* stream) {
+  return run(key_type, keys, vals, n, nullptr, 1, false, workspace, workspace_bytes, (cudaStream_t)stream,
+             nullptr);
+}
+
+ps_status ps_sort(int key_type, void* keys, uint32_t* vals, int64_t n, void* stream) {
+  return with_pool(key_type, keys, vals, n, nullptr, 1, false, (cudaStream_t)stream, nullptr);
+}
+
+ps_status ps_sort_i32(int32_t* keys, uint32_t* vals, int64_t n, void* stream) {
+  return ps_sort(PS_KEY_I32, keys, vals, n, stream);
+}
+ps_status ps_sort_u32(uint32_t* keys, uint32_t* vals, int64_t n, void* stream) {
+  return ps_sort(PS_KEY_U32, keys, vals, n, stream);
+}
+ps_status ps_sort_u64(uint64_t* keys, uint32_t* vals, int64_t n, void* stream) {
+  return ps_sort(PS_KEY_U64, keys, vals, n, stream);
+}
+ps_status ps_sort_f32(float* keys, uint32_t* vals, int64_t n, void* stream) {
+  return ps_sort(PS_KEY_F32, keys, vals, n, stream);
+}
+
+ps_status ps_sort_segmented_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                               int64_t count, void* workspace, size_t workspace_bytes, void* stream) {
+  return run(key_type, keys, vals, n, d_offsets, count, true, workspace, workspace_bytes, (cudaStream_t)stream,
+             nullptr);
+}
+
+ps_status ps_sort_segmented(int key_type, void* keys, uint32_t* vals, const int64_t* d_offsets, int64_t count,
+                            void* stream) {
+  if (!d_offsets || count < 1) return PS_ERR_INVALID_ARG;
+  int64_t n = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  PS_TRY(cudaMemcpyAsync(&n, d_offsets + count, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+  PS_TRY(cudaStreamSynchronize(s));
+  return with_pool(key_type, keys, vals, n, d_offsets, count, true, s, nullptr);
+}
+
+ps_status ps_merge_cost(const int64_t* run_lengths, int64_t r, uint64_t* out_cost) {
+  if (!run_lengths || !out_cost || r <= 0) return PS_ERR_INVALID_ARG;
+  return host_merge_cost(run_lengths, r, out_cost);
+}
+
+ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
+                     void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
+                     int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                     int32_t* node_right, uint8_t* node_depth, void* stream) {
+  AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
+  const bool seg = d_offsets != nullptr;
+  return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
+             workspace_bytes, (cudaStream_t)stream, &an);
+}
+
+ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream) {
+  if (!out) return PS_ERR_INVALID_ARG;
+  AnalyzeOut an{nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, out};
+  return with_pool(key_type, const_cast<void*>(keys), nullptr, n, nullptr, 1, false, (cudaStream_t)stream, &an);
+}
+
+ps_status ps_stream_status(void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return PS_ERR_CUDA;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PS_ERR_CUDA;
+  uint32_t* w = lib_status_word(dev);
+  if (!w) return PS_ERR_CUDA;
+  uint32_t v = 0;
+  if (cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PS_ERR_CUDA;
+  if (v) {
+    if (cudaMemset(w, 0, 4) != cudaSuccess) return PS_ERR_CUDA;
+    if (v & kDevTimeout) return PS_ERR_TIMEOUT;
+    return PS_ERR_INTERNAL;
+  }
+  return PS_OK;
+}
+
+const char* ps_status_string(ps_status status) {
+  switch (status) {
+    case PS_OK: return "ok";
+    case PS_ERR_INVALID_ARG: return "invalid argument";
+    case PS_ERR_UNSUPPORTED: return "unsupported size (n >= 2^31)";
+    case PS_ERR_OUT_OF_MEMORY: return "out of device memory / workspace too small";
+    case PS_ERR_CUDA: return "CUDA runtime error";
+    case PS_ERR_TIMEOUT: return "a bounded device wait timed out";
+    case PS_ERR_INTERNAL: return "internal error";
+  }
+  return "unknown status";
+}
+
+int ps_version(void) { return 100; }
+
+}  // extern "C"

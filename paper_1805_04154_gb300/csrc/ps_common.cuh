@@ -1,0 +1,142 @@
+// Shared device definitions of the GB300 powersort library: key-order maps, tile constants,
+// the plan header that the device fills for the host, and inline-PTX helpers for mbarriers and
+// bulk (TMA) copies.  Everything here is sm_103a device code or plain host structs.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ps {
+
+// ---------------------------------------------------------------------------------------
+// Sizes.  Positions are int32: one call sorts fewer than 2^31 elements in total, which also
+// keeps every node power below 32 (Definition "Node Power": P <= floor(lg n) + 1).
+// ---------------------------------------------------------------------------------------
+constexpr int kMaxLevels = 32;  // powers and depths are < 32
+
+// Stage 1 (run detection): one CTA scans a tile of kDetectTile positions.
+constexpr int kDetectThreads = 256;
+constexpr int kDetectItems = 16;
+constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096
+
+// Stage 3 (nearest-smaller-value tree): 8 warps x 32 rounds x 32 boundaries per tile.
+constexpr int kTreeWarps = 8;
+constexpr int kTreeRounds = 32;
+constexpr int kTreeTile = kTreeWarps * kTreeRounds * 32;  // 8192
+
+// Stage 4 (merge passes over HBM): one CTA produces kMergeTile outputs of one merge.
+constexpr int kMergeThreads = 256;
+constexpr int kMergeItems = 16;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;  // 4096
+
+// Stage 4 (whole small subtrees in shared memory): a tree node whose range holds at most
+// sub_tile(key size) elements is merged completely inside one CTA.
+constexpr int kSubThreads = 256;
+__host__ __device__ constexpr int sub_tile(int key_bytes) { return key_bytes == 8 ? 2048 : 4096; }
+
+// ---------------------------------------------------------------------------------------
+// Key orders.  Every key type is compared through an order-preserving map to an unsigned
+// integer: int32 flips the sign bit; float32 uses IEEE totalOrder (negative patterns are
+// complemented, non-negative ones get the sign bit set); unsigned types are themselves.
+// ---------------------------------------------------------------------------------------
+struct KeyI32 {
+  typedef uint32_t T;
+  static constexpr int kType = 0;
+  __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x ^ 0x80000000u; }
+};
+struct KeyU32 {
+  typedef uint32_t T;
+  static constexpr int kType = 1;
+  __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x; }
+};
+struct KeyU64 {
+  typedef uint64_t T;
+  static constexpr int kType = 2;
+  __device__ __forceinline__ static uint64_t ord(uint64_t x) { return x; }
+};
+struct KeyF32 {
+  typedef uint32_t T;
+  static constexpr int kType = 3;
+  __device__ __forceinline__ static uint32_t ord(uint32_t x) {
+    return x ^ ((uint32_t)((int32_t)x >> 31) | 0x80000000u);
+  }
+};
+
+// ---------------------------------------------------------------------------------------
+// Device-posted status bits (plan header and the library-wide status word).
+// ---------------------------------------------------------------------------------------
+enum DevStatus : uint32_t {
+  kDevOk = 0,
+  kDevTimeout = 1u << 0,      // a bounded wait gave up
+  kDevBadOffsets = 1u << 1,   // segment offsets not non-decreasing / out of range
+  kDevInternal = 1u << 2,     // an internal consistency check failed
+};
+
+// What the device tells the host after planning (one D2H copy per sort).
+struct PlanHeader {
+  int32_t runs;             // r: number of detected runs (all segments)
+  uint32_t status;          // DevStatus bits
+  uint32_t detect_ticket;   // dynamic tile counter of the detection scan
+  int32_t max_leaf_depth;
+  unsigned long long cost;  // merge cost M = sum of leaf depth x run length
+  uint32_t n_small;         // subtree-in-SMEM tasks
+  uint32_t pad0;
+  unsigned long long leaf_ctr;               // (count << 32) | tiles of large-leaf placement
+  unsigned long long level_ctr[kMaxLevels];  // per depth: (count << 32) | merge tiles
+};
+
+// One merge tile of a level pass: output [g0, next tile's g0 or hi) of the merge of
+// [lo, mid) and [mid, hi); i0 = elements taken from the left run before g0.
+struct TileDesc {
+  int32_t lo, mid, hi, g0, i0, pad[3];
+};
+
+// ---------------------------------------------------------------------------------------
+// PTX helpers (sm_90+ mbarrier / bulk async copies; used on sm_103a).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// 1-D bulk copy global -> shared, completion counted on an mbarrier.  Both addresses and the
+// size must be multiples of 16 bytes.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Post status bits to the per-call plan header and to the library's per-device status word
+// (read and cleared by ps_stream_status); either pointer may be null.
+__device__ __forceinline__ void post_status(uint32_t* hdr_status, uint32_t* lib_status, uint32_t bits) {
+  if (hdr_status) atomicOr(hdr_status, bits);
+  if (lib_status) atomicOr(lib_status, bits);
+}
+
+// Bounded waits: iterations before a wait gives up and posts kDevTimeout.  Look-back polls
+// sleep 64 ns between reads (about 0.3 s in all); an mbarrier try_wait suspends for a
+// hardware-defined interval per call.
+constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kMbarTries = 1u << 20;
+
+}  // namespace ps

@@ -1,0 +1,69 @@
+// Host-side internals shared by the library's translation units: the per-call context (device
+// pointers carved from the workspace) and the launcher entry points of each stage.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ps_common.cuh"
+
+namespace ps {
+
+struct Ctx {
+  cudaStream_t stream = nullptr;
+  int kt = 0;            // key type (powersort.h ps_key_type)
+  int key_bytes = 4;
+  bool has_vals = false;
+  int32_t n = 0;         // elements (all segments)
+  const int64_t* offsets = nullptr;  // device, count+1 entries, or null for one array
+  int32_t count = 1;
+
+  void* k[2] = {nullptr, nullptr};   // [0] caller's keys, [1] scratch keys
+  uint32_t* v[2] = {nullptr, nullptr};
+
+  // per-run / per-boundary metadata (capacity n + 2)
+  int32_t* S = nullptr;         // run starts, S[r] = n
+  uint8_t* run_desc = nullptr;  // run was strictly descending
+  int32_t* run_seg = nullptr;   // segment of each run (segmented calls only)
+  uint8_t* P = nullptr;         // node power of boundary j (0 for sentinels / segment borders)
+  int32_t* nodeL = nullptr;     // node j merges [S[nodeL[j]], S[j]) and [S[j], S[nodeR[j]])
+  int32_t* nodeR = nullptr;
+  uint8_t* ndepth = nullptr;    // node depth
+  uint8_t* ldepth = nullptr;    // leaf depth
+
+  uint64_t* detect_state = nullptr;
+  int32_t detect_tiles = 0;
+  int32_t* tree_sum = nullptr;  // [tree tiles][32]
+  int32_t* tree_pre = nullptr;
+
+  int32_t sub_lim = 0;          // subtree-in-SMEM element limit
+  int32_t* small_tasks = nullptr;
+  int32_t* leaf_items = nullptr;
+  uint32_t* leaf_tile_off = nullptr;
+  int32_t* level_items = nullptr;      // [kMaxLevels][level_cap]
+  uint32_t* level_tile_off = nullptr;
+  int32_t level_cap = 0;
+  TileDesc* tiles = nullptr;
+  int32_t tiles_cap = 0;
+
+  PlanHeader* hdr = nullptr;
+  uint32_t* lib_status = nullptr;  // per-device status word owned by the library
+  double* d_entropy = nullptr;
+};
+
+// Key-dependent stages (one table per key type).
+struct KeyLaunch {
+  cudaError_t (*detect)(const Ctx&);
+  cudaError_t (*small)(const Ctx&, uint32_t ntasks);
+  cudaError_t (*place)(const Ctx&, uint32_t nitems, uint32_t ntiles);
+  cudaError_t (*level)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
+};
+extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
+
+// Key-independent stages (ps_meta.cu).
+cudaError_t launch_meta_stages(const Ctx& c);
+cudaError_t launch_entropy(const Ctx& c, double* d_out);
+cudaError_t launch_check_offsets(const Ctx& c);
+
+}  // namespace ps

@@ -1,0 +1,364 @@
+// Stages 2-3 and planning: node powers, the merge tree as nearest smaller values of the powers,
+// node/leaf depths, merge cost, and the work lists of stage 4.  Key-independent; O(r) work.
+#include "ps_internal.h"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------------------
+// Stage 2: node power of every boundary (Definition "Node Power"; NodePower of Alg. 2).
+// Boundary j (1 <= j <= r-1) separates run j-1 = [S[j-1], S[j]) and run j = [S[j], S[j+1]).
+// With positions relative to the segment start and ns the segment length, the normalised
+// midpoints are a = (S[j-1]+S[j]) / (2 ns) and b = (S[j]+S[j+1]) / (2 ns); the power is the
+// index of their first differing fractional bit.  Since ns < 2^31, b - a >= 1/ns > 2^-31, so
+// the first 31 fractional bits decide it: x = floor(a 2^31), y = floor(b 2^31) (< 2^31), and
+// the power is the number of leading zeros of x ^ y in 32 bits.  Boundaries between segments
+// and the sentinels j = 0, j = r get power 0 (smaller than every real power).
+// ---------------------------------------------------------------------------------------
+__global__ void node_power_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ run_seg,
+                                  const int64_t* __restrict__ offsets, int32_t n, uint8_t* __restrict__ P,
+                                  const PlanHeader* __restrict__ hdr) {
+  const int32_t r = hdr->runs;
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= r; j += gridDim.x * blockDim.x) {
+    uint8_t p = 0;
+    if (j >= 1 && j < r) {
+      int64_t base = 0, ns = n;
+      bool same = true;
+      if (run_seg != nullptr) {
+        const int32_t sg = run_seg[j];
+        same = (run_seg[j - 1] == sg);
+        base = offsets[sg];
+        ns = offsets[sg + 1] - base;
+        if (ns <= 0) same = false;  // only with invalid offsets, which the host rejects
+      }
+      if (same) {
+        const uint64_t l2 = (uint64_t)((int64_t)S[j - 1] + S[j] - 2 * base);
+        const uint64_t r2 = (uint64_t)((int64_t)S[j] + S[j + 1] - 2 * base);
+        const uint64_t two_n = (uint64_t)(2 * ns);
+        const uint32_t x = (uint32_t)((l2 << 31) / two_n);
+        const uint32_t y = (uint32_t)((r2 << 31) / two_n);
+        p = (uint8_t)min(__clz(x ^ y), 31);
+      }
+    }
+    P[j] = p;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Stage 3: the merge tree (Corollary "Cartesian tree": the min-Cartesian tree of the powers).
+// For node j: Lj = nearest i < j with P_i < P_j, Rj = nearest k > j with P_k < P_j (the
+// power-0 sentinels and segment boundaries always qualify); node j merges [S[Lj], S[j]) with
+// [S[j], S[Rj]).  Its ancestors are exactly the "records" on either side: a boundary i < j is
+// an ancestor iff P_i is smaller than every power strictly between i and j and than P_j.  Among
+// positions of one power value only the last one before j can be a record, so with last[v] =
+// last index before j holding power v, the left ancestors are the v in [1, P_j) with
+// last[v] > max(last[0..v-1]), and Lj = max(last[0..P_j-1]).  The right side is the same on
+// reversed indices.  depth(j) = left records + right records (powers are < 32, so the 32
+// last[] entries live one per lane of a warp).
+//
+// The scan over last[] vectors runs in three kernels per direction: per-tile summaries, an
+// exclusive max-scan over tiles, and the apply pass.  Virtual index u maps to boundary
+// j = u (forward) or j = r - u (backward).
+// ---------------------------------------------------------------------------------------
+template <bool kBackward>
+__device__ __forceinline__ int32_t virt_to_j(int32_t u, int32_t r) {
+  return kBackward ? r - u : u;
+}
+
+// Per-warp pass over kTreeRounds rounds of 32 virtual indices starting at u0.  Updates carry
+// (lane v = last virtual index < current with power v, or -1).  If kApply, also emits L/R and
+// record counts for every node.
+template <bool kBackward, bool kApply>
+__device__ __forceinline__ void tree_warp_rounds(const uint8_t* __restrict__ P, int32_t r, int32_t u0,
+                                                 int32_t& carry, int32_t* __restrict__ near_out,
+                                                 uint8_t* __restrict__ depth_acc) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < kTreeRounds; ++round) {
+    const int32_t ub = u0 + round * 32;
+    if (ub > r) break;
+    const int32_t u = ub + lane;
+    const bool valid = u <= r;
+    const int32_t j = virt_to_j<kBackward>(u, r);
+    const int p = valid ? (int)P[j] : 0;
+    const int maxp = __reduce_max_sync(0xffffffffu, valid ? p : 0);
+    const uint32_t lt = (1u << lane) - 1u;
+    int32_t M = -1, cnt = 0;
+    uint32_t myb = 0;
+    for (int v = 0; v <= maxp; ++v) {
+      const uint32_t b = __ballot_sync(0xffffffffu, valid && p == v);
+      if (lane == v) myb = b;
+      if (kApply) {
+        const int32_t cv = __shfl_sync(0xffffffffu, carry, v);
+        const uint32_t bl = b & lt;
+        const int32_t lastv = bl ? ub + 31 - __clz(bl) : cv;
+        if (v < p) {
+          if (v >= 1 && lastv > M) ++cnt;
+          M = max(M, lastv);
+        }
+      }
+    }
+    if (kApply && valid && p >= 1) {
+      const int32_t nearest = virt_to_j<kBackward>(M, r);
+      near_out[j] = nearest;
+      if (kBackward)
+        depth_acc[j] = (uint8_t)(depth_acc[j] + cnt);
+      else
+        depth_acc[j] = (uint8_t)cnt;
+    }
+    if (myb) carry = ub + 31 - __clz(myb);
+  }
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(kTreeWarps * 32)
+tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr, int32_t* __restrict__ summary) {
+  __shared__ int32_t sw[kTreeWarps][32];
+  const int32_t r = hdr->runs;
+  const int32_t ntiles = r / kTreeTile + 1;  // virtual indices 0..r
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int32_t carry = -1;
+    tree_warp_rounds<kBackward, false>(P, r, t * kTreeTile + warp * kTreeRounds * 32, carry, nullptr, nullptr);
+    sw[warp][lane] = carry;
+    __syncthreads();
+    if (warp == 0) {
+      int32_t m = -1;
+      for (int w = 0; w < kTreeWarps; ++w) m = max(m, sw[w][lane]);
+      summary[t * 32 + lane] = m;
+    }
+    __syncthreads();
+  }
+}
+
+// exclusive max-scan over tiles, one warp per power value (grid: 1 block of 32 warps)
+__global__ void __launch_bounds__(1024)
+tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__ summary, int32_t* __restrict__ prefix) {
+  const int32_t r = hdr->runs;
+  const int32_t ntiles = r / kTreeTile + 1;
+  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  int32_t run = -1;
+  for (int32_t base = 0; base < ntiles; base += 32 * 4) {
+    int32_t x[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int32_t t = base + q * 32 + lane;
+      x[q] = t < ntiles ? summary[t * 32 + v] : -1;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int32_t inc = x[q];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc = max(inc, o);
+      }
+      int32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+      if (lane == 0) exc = -1;
+      const int32_t t = base + q * 32 + lane;
+      if (t < ntiles) prefix[t * 32 + v] = max(run, exc);
+      run = max(run, __shfl_sync(0xffffffffu, inc, 31));
+    }
+  }
+}
+
+template <bool kBackward>
+__global__ void __launch_bounds__(kTreeWarps * 32)
+tree_apply_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr,
+                  const int32_t* __restrict__ prefix, int32_t* __restrict__ near_out,
+                  uint8_t* __restrict__ depth_acc) {
+  __shared__ int32_t sw[kTreeWarps][32];
+  const int32_t r = hdr->runs;
+  const int32_t ntiles = r / kTreeTile + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int32_t u0 = t * kTreeTile + warp * kTreeRounds * 32;
+    int32_t c = -1;
+    tree_warp_rounds<kBackward, false>(P, r, u0, c, nullptr, nullptr);
+    sw[warp][lane] = c;
+    __syncthreads();
+    int32_t carry = prefix[t * 32 + lane];
+    for (int w = 0; w < warp; ++w) carry = max(carry, sw[w][lane]);
+    tree_warp_rounds<kBackward, true>(P, r, u0, carry, near_out, depth_acc);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Planning.  Leaf i (run i) hangs below the adjacent boundary with the larger power (i or
+// i+1); its depth is that node's depth + 1, or 0 when the run is a whole segment.  Stage 4 is
+// organised around the element count sub_lim that one CTA can merge in shared memory:
+//  * a node or leaf of size <= sub_lim whose parent is larger (or that is a root) is one
+//    "small task": its whole subtree is merged in shared memory;
+//  * larger leaves that must move (odd depth -> scratch buffer, or descending -> reversed) get
+//    placement tiles;
+//  * larger internal nodes are merged by HBM passes, one pass per depth.
+// Buffer parity: a node at depth d writes buffer d mod 2 (0 = the caller's arrays) and reads
+// its children from buffer (d+1) mod 2, so every leaf starts in buffer (depth mod 2).
+// M = sum over leaves of depth x length (Sec. 2.3).
+// ---------------------------------------------------------------------------------------
+__global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+                            const uint8_t* __restrict__ P, const int32_t* __restrict__ nodeL,
+                            const int32_t* __restrict__ nodeR, const uint8_t* __restrict__ ndepth,
+                            uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
+                            int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
+                            int32_t* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
+                            int32_t level_cap, int32_t small_cap, PlanHeader* __restrict__ hdr) {
+  const int32_t r = hdr->runs;
+  unsigned long long cost = 0;
+  int32_t maxd = 0;
+  auto node_size = [&](int32_t j) -> int32_t { return S[nodeR[j]] - S[nodeL[j]]; };
+  auto node_parent = [&](int32_t j) -> int32_t {
+    const int32_t L = nodeL[j], R = nodeR[j];
+    const int pl = P[L], pr = P[R];
+    if (pl == 0 && pr == 0) return -1;
+    return pl > pr ? L : R;
+  };
+  for (int32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < r; x += gridDim.x * blockDim.x) {
+    // leaf x
+    {
+      const int pl = P[x], pr = P[x + 1];
+      const int32_t par = (pl == 0 && pr == 0) ? -1 : (pl > pr ? x : x + 1);
+      const int32_t d = par < 0 ? 0 : ndepth[par] + 1;
+      ldepth[x] = (uint8_t)d;
+      maxd = max(maxd, d);
+      const int32_t len = S[x + 1] - S[x];
+      cost += (unsigned long long)d * (unsigned long long)len;
+      if (len <= sub_lim) {
+        if (par < 0 || node_size(par) > sub_lim) {
+          const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
+          if (slot < (uint32_t)small_cap) small_tasks[slot] = ~x;  // leaf task
+          else post_status(&hdr->status, nullptr, kDevInternal);
+        }
+      } else {
+        const bool desc = run_desc[x] != 0;
+        uint32_t tiles = 0;
+        if (d & 1) tiles = (uint32_t)((len + kMergeTile - 1) / kMergeTile);
+        else if (desc) tiles = (uint32_t)((len / 2 + kMergeTile - 1) / kMergeTile);
+        if (tiles) {
+          const unsigned long long old = atomicAdd(&hdr->leaf_ctr, (1ull << 32) | tiles);
+          const uint32_t slot = (uint32_t)(old >> 32);
+          if (slot < (uint32_t)level_cap) {
+            leaf_items[slot] = x;
+            leaf_tile_off[slot] = (uint32_t)(old & 0xffffffffu);
+          } else {
+            post_status(&hdr->status, nullptr, kDevInternal);
+          }
+        }
+      }
+    }
+    // node x (boundary between runs x-1 and x)
+    if (x >= 1 && P[x] >= 1) {
+      const int32_t lo = S[nodeL[x]], hi = S[nodeR[x]];
+      const int32_t size = hi - lo;
+      const int32_t par = node_parent(x);
+      if (size <= sub_lim) {
+        if (par < 0 || node_size(par) > sub_lim) {
+          const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
+          if (slot < (uint32_t)small_cap) small_tasks[slot] = x;
+          else post_status(&hdr->status, nullptr, kDevInternal);
+        }
+      } else {
+        const int d = ndepth[x];
+        const uint32_t tiles = (uint32_t)((hi - 1) / kMergeTile - lo / kMergeTile + 1);
+        if (d >= kMaxLevels) {
+          post_status(&hdr->status, nullptr, kDevInternal);
+        } else {
+          const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
+          const uint32_t slot = (uint32_t)(old >> 32);
+          if (slot < (uint32_t)level_cap) {
+            level_items[(size_t)d * level_cap + slot] = x;
+            level_tile_off[(size_t)d * level_cap + slot] = (uint32_t)(old & 0xffffffffu);
+          } else {
+            post_status(&hdr->status, nullptr, kDevInternal);
+          }
+        }
+      }
+    }
+  }
+  // block reductions of cost and max depth
+  __shared__ unsigned long long s_cost;
+  __shared__ int32_t s_maxd;
+  if (threadIdx.x == 0) {
+    s_cost = 0;
+    s_maxd = 0;
+  }
+  __syncthreads();
+  for (int d = 16; d >= 1; d >>= 1) {
+    cost += __shfl_down_sync(0xffffffffu, cost, d);
+    maxd = max(maxd, __shfl_down_sync(0xffffffffu, maxd, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&s_cost, cost);
+    atomicMax(&s_maxd, maxd);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(&hdr->cost, s_cost);
+    atomicMax(&hdr->max_leaf_depth, s_maxd);
+  }
+}
+
+// Sum over runs of L * log2(L) and per-segment n * log2(n) pieces for the entropy statistic:
+// n H = sum_segments n_s lg n_s - sum_runs L lg L.  (Statistic only; not on the sort path.)
+__global__ void entropy_kernel(const int32_t* __restrict__ S, const PlanHeader* __restrict__ hdr, double* out) {
+  const int32_t r = hdr->runs;
+  double acc = 0.0;
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) {
+    const double L = (double)(S[i + 1] - S[i]);
+    acc += L * (double)log2f((float)L);
+  }
+  for (int d = 16; d >= 1; d >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, d);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
+// Segment offsets must start at 0, be non-decreasing and end at n.
+__global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int32_t count, int64_t n,
+                                     PlanHeader* __restrict__ hdr) {
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= count; k += gridDim.x * blockDim.x) {
+    bool bad = false;
+    if (k == 0) bad = offsets[0] != 0;
+    else bad = offsets[k] < offsets[k - 1];
+    if (k == count) bad = bad || offsets[k] != n;
+    if (bad) post_status(&hdr->status, nullptr, kDevBadOffsets);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers for the key-independent stages.
+// ---------------------------------------------------------------------------------------
+static int persistent_blocks(int per_sm) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 152;
+  }
+  return sms * per_sm;
+}
+
+cudaError_t launch_meta_stages(const Ctx& c) {
+  const int grid = persistent_blocks(8);
+  node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
+  tree_summary_kernel<false><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_sum);
+  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
+  tree_apply_kernel<false><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeL, c.ndepth);
+  tree_summary_kernel<true><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_sum);
+  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
+  tree_apply_kernel<true><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeR, c.ndepth);
+  plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
+                                          c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
+                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_entropy(const Ctx& c, double* d_out) {
+  entropy_kernel<<<persistent_blocks(4), 256, 0, c.stream>>>(c.S, c.hdr, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_check_offsets(const Ctx& c) {
+  check_offsets_kernel<<<persistent_blocks(1), 256, 0, c.stream>>>(c.offsets, c.count, c.n, c.hdr);
+  return cudaGetLastError();
+}
+
+}  // namespace ps

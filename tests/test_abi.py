@@ -1,0 +1,82 @@
+"""CPU checks of the C ABI: the library loads, exports every function include/*.h declares,
+rejects bad arguments before touching a GPU, and its host-only merge cost agrees with the
+oracle."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import ROOT
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1805_04154_gb300 as ps
+    from paper_1805_04154_gb300 import _build
+    _build.build()
+    return ps.load()
+
+
+def _declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(ps_[a-z0-9_]+)\s*\(",
+                            text, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for want in ("ps_sort", "ps_sort_segmented", "ps_merge_cost", "ps_sort_stats", "ps_stream_status",
+                 "ps_status_string", "ps_analyze", "ps_sort_ws", "ps_workspace_size"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_status_strings(lib):
+    import paper_1805_04154_gb300 as ps
+    for s in range(7):
+        assert len(ps.ps_status_string(s)) > 0
+    assert ps.ps_version() >= 100
+
+
+def test_argument_errors_without_gpu(lib):
+    ws = ctypes.c_void_p(256)
+    # unknown key type, negative n, misaligned pointer, too large n: rejected before any CUDA call
+    assert lib.ps_sort_ws(9, ctypes.c_void_p(4096), None, 10, ws, 1 << 20, None) == 1
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, -1, ws, 1 << 20, None) == 1
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4100), None, 10, ws, 1 << 20, None) == 1
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), ctypes.c_void_p(4104), 10, ws, 1 << 20, None) == 1
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1 << 31, ws, 1 << 20, None) == 2
+    assert lib.ps_workspace_size(0, 1, 1000, 0) > 1000 * 8
+    assert lib.ps_workspace_size(7, 1, 1000, 0) == 0
+    # n = 0 and n = 1 are no-ops
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 0, None, 0, None) == 0
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1, None, 0, None) == 0
+
+
+def test_merge_cost_host_matches_oracle(lib):
+    import paper_1805_04154_gb300 as ps
+    rng = np.random.default_rng(1)
+    assert ps.ps_merge_cost([5, 3, 3, 14, 1, 2]) == 67  # Fig. 1, Method 2 tree
+    for _ in range(300):
+        r = int(rng.integers(1, 300))
+        L = rng.integers(1, int(rng.choice([3, 100, 10 ** 6])), size=r)
+        assert ps.ps_merge_cost(L) == oracle.powersort_cost(L)[0]
+    # large n beyond 2^31 still exact (62-bit formulation)
+    L = rng.integers(1, 1 << 40, size=50)
+    assert ps.ps_merge_cost(L) == oracle.powersort_cost(L)[0]
+    out = ctypes.c_uint64()
+    bad = np.array([3, 0, 2], np.int64)
+    assert lib.ps_merge_cost(ctypes.c_void_p(bad.ctypes.data), 3, ctypes.byref(out)) == 1
+    assert lib.ps_merge_cost(None, 3, ctypes.byref(out)) == 1
