@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 powersort path.
+
+Workload: n = 10^8 int32 keys with a uint32 payload (the original index), made of runs whose
+lengths are uniform in [1, 2 sqrt(n)] = [1, 20000], each run filled with sorted uniform-random
+int32 values and 25% of runs reversed (descending).  Seeded and synthetic.  One step = one full
+stable sort of one such array (run detection, node powers, merge tree, all merges).
+
+GB300 arm (default): every step sorts its own resident device copy (800 MB of keys + payload,
+larger than the 129 MB L2), so nothing is reused across steps; K steps are timed with CUDA
+events between a barrier + synchronize on both sides, max over ranks.  Also reported:
+  * roofline  -- the merge-tile kernel (the dominant one): algorithmic bytes (2 x elements x 8 B
+                 per merge output) over its CUDA-event time inside the timed region, against the
+                 measured HBM copy bandwidth; plus the whole sort against the merge-cost
+                 roofline M x 8 B x 2 / bandwidth (M = exact merge cost of the detected runs).
+  * e2e       -- the same metric through the C-ABI host-buffer entry (ps_sort_host): pinned host
+                 input -> device, sort, device -> pinned host output, every step.
+  * cpu_baseline -- the CPU oracle (single-threaded plain C++ powersort) on one input of the same
+                 workload on the host cores.
+--impl reference: the oracle as the reference arm, each step a bounded sample (the first
+10^7 keys of the same workload).
+Multi-GPU (torchrun): independent replicas, one array per rank, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GKeys/s and % of HBM merge-cost roofline; batched/served vs plain; p50/p99 latency"
+UNIT = "GKeys/s"
+N_DEFAULT = 10 ** 8
+SEED = 42
+WORKLOAD = "plain powersort, n=1e8 int32 keys + uint32 payload, run lengths uniform in [1, 2*sqrt(n)], " \
+           "sorted uniform int32 per run, 25% of runs descending"
+FALLBACK_HBM_GBS = 6800.0
+REF_SAMPLE = 10 ** 7
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None, period_ms: int = 50):
+        import tempfile
+        self.proc = None
+        fd, self.path = tempfile.mkstemp(prefix="ps_clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", f"-lms={period_ms}"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]), "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows if r[3][0].isdigit())}
+
+
+def _gen(n: int, seed: int):
+    import numpy as np
+    import workloads
+    max_len = max(1, int(2 * np.sqrt(N_DEFAULT if n == N_DEFAULT else n)))
+    return workloads.runs_i32(n, seed, max_len=max_len)
+
+
+def _cpu_baseline(keys, vals, sample_desc: str):
+    import oracle
+    t = time.perf_counter()
+    res = oracle.powersort(keys, vals)
+    dt = time.perf_counter() - t
+    return {"value": keys.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads
+    oracle.build()
+    workloads.build()
+    n_s = min(REF_SAMPLE, args.n)
+    keys, vals = workloads.runs_i32(n_s, SEED, max_len=int(2 * (args.n ** 0.5)))
+    import numpy as np
+    for _ in range(args.warmup):
+        oracle.powersort(keys, vals)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.powersort(keys, vals)
+        times.append(time.perf_counter() - t)
+    total = sum(times)
+    value = n_s * args.steps / total / 1e9
+    sample = f"first {n_s} keys of the n={args.n} workload (same seed and run-length law), per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "sample_n": n_s,
+                       "parallelism": "replicas (reference runs on rank 0 only)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_1805_04154_gb300 import _build
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    import paper_1805_04154_gb300 as ps
+    ps.load()
+    import oracle
+
+    n = args.n
+    keys, vals = _gen(n, SEED + rank)
+    eb = 8
+    dk0 = torch.from_numpy(keys).to(dev)
+    dv0 = torch.from_numpy(vals.view(np.int32)).to(dev)
+    an = ps.ps_analyze(dk0, key_type=ps.PS_KEY_I32)
+    M = an["cost"]
+    lengths = np.diff(an["starts"]).astype(np.float64)
+    H = float(-(lengths / n * np.log2(lengths / n)).sum())
+
+    # one resident copy per step (each step sorts fresh data; inputs > L2)
+    free, _ = torch.cuda.mem_get_info(dev)
+    per_copy = n * eb
+    wsb = ps.ps_workspace_size(ps.PS_KEY_I32, True, n)
+    fit = max(1, int((free - wsb - (4 << 30)) // per_copy))
+    ncopies = min(args.steps + args.warmup, fit)
+    copies = [(dk0.clone(), dv0.clone()) for _ in range(ncopies)]
+    workspace = torch.empty(wsb, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i):
+        k, v = copies[i]
+        ps.ps_sort_ws(k, v, workspace, key_type=ps.PS_KEY_I32, stream=stream)
+
+    def restore(lo, hi):
+        for i in range(lo, hi):
+            copies[i][0].copy_(dk0)
+            copies[i][1].copy_(dv0)
+
+    # warm-up
+    for w in range(args.warmup):
+        step(w % ncopies)
+    torch.cuda.synchronize(dev)
+    restore(0, ncopies)
+    torch.cuda.synchronize(dev)
+
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if gpu_id and not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = None
+    sampler = ClockSampler(gpu_id)
+    time.sleep(0.15)
+
+    # timed region: chunks of at most ncopies steps; restores happen between chunks, outside
+    ps.ps_profile_enable(True)
+    launches0 = ps.ps_launch_count()
+    total_ms = 0.0
+    done = 0
+    while done < args.steps:
+        chunk = min(ncopies, args.steps - done)
+        if done > 0:
+            restore(0, chunk)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(chunk):
+            step(i)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        total_ms += e0.elapsed_time(e1)
+        done += chunk
+    launches = ps.ps_launch_count() - launches0
+    prof = ps.ps_profile_read()
+    ps.ps_profile_enable(False)
+    clocks = sampler.stop()
+    assert ps.ps_stream_status() == 0, "device reported an error"
+
+    # correctness of the timed outputs (cheap device-side checks on the last copy)
+    k, v = copies[(args.steps - 1) % ncopies]
+    ok = bool((k[1:] >= k[:-1]).all().item())
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = ws * n * args.steps / (total_ms / 1000.0) / 1e9
+
+    peak, peak_kind = _peaks()
+    mt = prof["merge_tile"]
+    achieved = (mt["bytes"] / (mt["ms"] / 1000.0) / 1e9) if mt["ms"] > 0 else None
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "merge_tile_traffic.json")
+    if os.path.exists(tpath):
+        try:
+            import hashlib
+            with open(tpath) as f:
+                tr = json.load(f)
+            src = open(os.path.join(ROOT, "paper_1805_04154_gb300", "csrc", "ps_merge.cuh"), "rb").read()
+            if tr.get("source_sha256") == hashlib.sha256(src).hexdigest() and mt["launches"]:
+                elems_per_launch = mt["bytes"] / (2 * eb) / mt["launches"]
+                traffic = tr["dram_bytes_per_output_elem"] * elems_per_launch
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": "merge_tile_kernel", "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "peak_kind": peak_kind,
+                "launches": mt["launches"], "ms_total": mt["ms"], "algorithmic_bytes_total": mt["bytes"]}
+    ideal_ms = M * eb * 2 / (peak * 1e9) * 1000.0
+    merge_cost_roofline = {"M": int(M), "bytes_per_step": int(M * eb * 2), "ideal_ms": ideal_ms,
+                           "frac": ideal_ms / ms_per_step, "nH": H * n, "peak_gbs": peak}
+    stages_ms = {k2: round(v2["ms"] / args.steps, 4) for k2, v2 in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": n, "key": "int32", "payload": "uint32",
+                       "run_lengths": f"uniform [1, {int(2 * N_DEFAULT ** 0.5) if n == N_DEFAULT else int(2 * n ** 0.5)}]",
+                       "desc_frac": 0.25, "seed": SEED,
+                       "l2": "no flush: every step sorts its own resident 800 MB copy (> 129 MB L2)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": roofline, "merge_cost_roofline": merge_cost_roofline,
+            "plan": {"runs": int(an["runs"]), "merge_cost": int(M), "entropy_bits": H,
+                     "max_leaf_depth": int(an["leaf_depth"].max())},
+            "stages_ms_per_step": stages_ms, "gpu_launches": int(launches), "clocks": clocks,
+            "sorted_check": ok}
+
+    # end to end through the C ABI with host buffers (pinned), every step H2D + sort + D2H
+    if not args.no_e2e:
+        hk_in = torch.from_numpy(keys).pin_memory()
+        hv_in = torch.from_numpy(vals.view(np.int32)).pin_memory()
+        hk_out = torch.empty_like(hk_in).pin_memory()
+        hv_out = torch.empty_like(hv_in).pin_memory()
+        e2e_steps = max(3, min(args.steps, 10))
+        for _ in range(2):
+            ps.ps_sort_host_ptr(ps.PS_KEY_I32, hk_in.data_ptr(), hv_in.data_ptr(), hk_out.data_ptr(),
+                                hv_out.data_ptr(), n, stream=stream)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            ps.ps_sort_host_ptr(ps.PS_KEY_I32, hk_in.data_ptr(), hv_in.data_ptr(), hk_out.data_ptr(),
+                                hv_out.data_ptr(), n, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": ws * n * e2e_steps / (e2e_ms / 1000.0) / 1e9, "unit": UNIT,
+                       "h2d_bytes_per_step": n * eb, "d2h_bytes_per_step": n * eb, "steps": e2e_steps,
+                       "ms_per_step": e2e_ms / e2e_steps, "entry": "ps_sort_host (pinned host buffers)"}
+        ok_e2e = bool(np.all(hk_out.numpy()[1:] >= hk_out.numpy()[:-1]))
+        line["e2e"]["sorted_check"] = ok_e2e
+
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = _cpu_baseline(keys, vals, f"one full n={n} input of the same workload, "
+                                                         "oracle powersort (Alg. 2), single thread")
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--n", type=int, default=N_DEFAULT, help="array size (default 1e8)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -133,6 +133,31 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
  * Synchronizes the stream. */
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream);
 
+/* Sort host arrays through the GPU: copies keys_in/vals_in (host, n elements; pinned memory gives
+ * the fastest copies) to device buffers from the library's pool, sorts them as ps_sort does, and
+ * copies the result to keys_out/vals_out (host; may alias the inputs).  vals_in and vals_out
+ * are both NULL or both non-NULL.  Synchronizes the stream before returning. */
+ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                       uint32_t* vals_out, int64_t n, void* stream);
+
+/* Measurement.  While enabled, every sort records CUDA events on its stream around its stages
+ * (0 run detection, 1 node powers + merge tree + plan, 2 subtrees merged in shared memory,
+ * 3 large-leaf placement, 4 co-rank search, 5 merge tiles of the level passes).
+ * ps_profile_read waits for the recorded events and returns, per stage since the last enable,
+ * the device milliseconds, kernel launches and algorithmic HBM bytes (every element a stage
+ * moves counted once read and once written: 2 x elements x (key bytes + payload bytes); run
+ * detection reads the keys once).  ps_profile_enable(on) also clears the accumulators. */
+typedef struct ps_profile {
+  double ms[8];
+  uint64_t launches[8];
+  uint64_t bytes[8];
+} ps_profile;
+ps_status ps_profile_enable(int on);
+ps_status ps_profile_read(ps_profile* out);
+
+/* Number of kernels the library has launched in this process (all devices, all calls). */
+uint64_t ps_launch_count(void);
+
 /* Synchronizes `stream`, then reports (and clears) errors the device posted on the current
  * device since the last call: PS_ERR_TIMEOUT if a bounded wait gave up, PS_ERR_CUDA if the
  * stream itself failed, else PS_OK. */

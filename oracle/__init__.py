@@ -122,13 +122,15 @@ def powersort(keys: np.ndarray, vals: np.ndarray | None = None, kt: str = "i32",
     v = None if vals is None else np.ascontiguousarray(vals, dtype=np.uint32).copy()
     n = k.size
     cap = n + 2
-    starts = np.zeros(cap, np.int64)
-    desc = np.zeros(cap, np.uint8)
-    power = np.zeros(cap, np.int32)
-    npar = np.full(cap, -1, np.int64)
-    lpar = np.full(cap, -1, np.int64)
-    ldep = np.zeros(cap, np.int32)
-    merges = np.zeros(3 * cap, np.int64)
+    # the C code writes every entry it defines (r+1 or r of them); np.empty keeps untouched
+    # capacity unallocated
+    starts = np.empty(cap, np.int64)
+    desc = np.empty(cap, np.uint8)
+    power = np.empty(cap, np.int32)
+    npar = np.empty(cap, np.int64)
+    lpar = np.empty(cap, np.int64)
+    ldep = np.empty(cap, np.int32)
+    merges = np.empty(3 * cap, np.int64)
     cost = ctypes.c_uint64(0)
     r = _load().ps_oracle_powersort(KT[kt], _p(k), _p(v), n, min_run, _p(starts), _p(desc),
                                     _p(power), _p(npar), _p(lpar), _p(ldep), _p(merges),

@@ -20,8 +20,11 @@ __all__ = [
     "PowersortError", "PS_KEY_I32", "PS_KEY_U32", "PS_KEY_U64", "PS_KEY_F32", "lib_path", "load",
     "ps_sort", "ps_sort_ws", "ps_sort_segmented", "ps_sort_segmented_ws", "ps_workspace_size",
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
-    "ps_version", "key_type_of",
+    "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
+    "ps_launch_count", "STAGES",
 ]
+
+STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "corank", "merge_tile"]
 
 PS_KEY_I32, PS_KEY_U32, PS_KEY_U64, PS_KEY_F32 = 0, 1, 2, 3
 _STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_OUT_OF_MEMORY",
@@ -31,6 +34,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 lib_path = os.path.join(_HERE, "libpowersort.so")
 _lib = None
 _lock = threading.Lock()
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_uint64 * 8),
+                ("bytes", ctypes.c_uint64 * 8)]
 
 
 class PowersortError(RuntimeError):
@@ -71,6 +79,10 @@ def load():
                 "ps_stream_status": ([vp], i32),
                 "ps_status_string": ([i32], ctypes.c_char_p),
                 "ps_version": ([], i32),
+                "ps_sort_host": ([i32, vp, vp, vp, vp, i64, vp], i32),
+                "ps_profile_enable": ([i32], i32),
+                "ps_profile_read": ([vp], i32),
+                "ps_launch_count": ([], u64),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(lib, name)
@@ -201,9 +213,9 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
     seg = offsets is not None
     ws = _workspace(ps_workspace_size(kt, False, n, seg), keys.device)
     cap = n + 2
-    out = {"starts": np.zeros(cap, np.int32), "desc": np.zeros(cap, np.uint8), "power": np.zeros(cap, np.uint8),
-           "leaf_depth": np.zeros(cap, np.uint8), "node_left": np.zeros(cap, np.int32),
-           "node_right": np.zeros(cap, np.int32), "node_depth": np.zeros(cap, np.uint8)}
+    out = {"starts": np.empty(cap, np.int32), "desc": np.empty(cap, np.uint8), "power": np.empty(cap, np.uint8),
+           "leaf_depth": np.empty(cap, np.uint8), "node_left": np.empty(cap, np.int32),
+           "node_right": np.empty(cap, np.int32), "node_depth": np.empty(cap, np.uint8)}
     runs = ctypes.c_int64(0)
     cost = ctypes.c_uint64(0)
     p = {k: ctypes.c_void_p(v.ctypes.data) for k, v in out.items()}
@@ -233,3 +245,41 @@ def ps_stream_status(stream=None, device=None) -> int:
     if stream is None:
         stream = torch.cuda.current_stream(device)
     return int(load().ps_stream_status(ctypes.c_void_p(stream.cuda_stream)))
+
+
+def ps_sort_host(keys_in: np.ndarray, vals_in: np.ndarray | None, keys_out: np.ndarray,
+                 vals_out: np.ndarray | None, key_type: int, stream=None) -> None:
+    """Sort host arrays through the GPU (copies in, sorts, copies out; synchronizes)."""
+    n = keys_in.size
+    for a in (keys_in, vals_in, keys_out, vals_out):
+        if a is not None and not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be contiguous")
+    sp = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
+    ptr = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
+    _check(load().ps_sort_host(key_type, ptr(keys_in), ptr(vals_in), ptr(keys_out), ptr(vals_out), n, sp),
+           "ps_sort_host")
+
+
+def ps_sort_host_ptr(key_type: int, keys_in: int, vals_in: int | None, keys_out: int, vals_out: int | None,
+                     n: int, stream=None) -> None:
+    """ps_sort_host on raw host addresses (e.g. pinned torch tensors' data_ptr())."""
+    sp = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
+    vp = (lambda a: None if a is None else ctypes.c_void_p(a))
+    _check(load().ps_sort_host(key_type, vp(keys_in), vp(vals_in), vp(keys_out), vp(vals_out), n, sp),
+           "ps_sort_host")
+
+
+def ps_profile_enable(on: bool = True) -> None:
+    _check(load().ps_profile_enable(1 if on else 0), "ps_profile_enable")
+
+
+def ps_profile_read() -> dict:
+    """Per stage: device ms, kernel launches, algorithmic HBM bytes since the last enable."""
+    p = _Profile()
+    _check(load().ps_profile_read(ctypes.byref(p)), "ps_profile_read")
+    return {name: {"ms": p.ms[i], "launches": int(p.launches[i]), "bytes": int(p.bytes[i])}
+            for i, name in enumerate(STAGES)}
+
+
+def ps_launch_count() -> int:
+    return int(load().ps_launch_count())

@@ -3,6 +3,7 @@
 //   detect runs -> node powers -> merge tree -> plan -> [one D2H of the plan header]
 //   -> small subtrees in SMEM + large-leaf placement -> level passes, deepest first.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -106,6 +107,45 @@ cudaMemPool_t lib_pool(int dev) {
   return g_pool[dev];
 }
 
+// ---- measurement: per-stage device time (CUDA events on the caller's stream), launches,
+// algorithmic bytes --------------------------------------------------------------------------
+constexpr int kStages = 8;  // 0 detect, 1 powers+tree+plan, 2 SMEM subtrees, 3 leaf placement,
+                            // 4 co-rank search, 5 merge tiles
+std::atomic<int> g_prof_on{0};
+std::atomic<unsigned long long> g_launches{0};
+struct ProfRec {
+  int stage;
+  cudaEvent_t a, b;
+  uint64_t bytes, launches;
+};
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof_pending;
+double g_prof_ms[kStages] = {};
+uint64_t g_prof_launch[kStages] = {}, g_prof_bytes[kStages] = {};
+
+struct StageTimer {
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  bool on;
+  StageTimer(int st, cudaStream_t strm) : stage(st), s(strm), on(g_prof_on.load() != 0) {
+    if (on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    else on = false;
+  }
+  void done(uint64_t bytes, uint64_t launches) {
+    g_launches += launches;
+    if (!on) return;
+    cudaEvent_t b = nullptr;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof_pending.push_back(ProfRec{stage, a, b, bytes, launches});
+  }
+};
+
 struct AnalyzeOut {
   int64_t* runs;
   uint64_t* cost;
@@ -179,12 +219,22 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
   PS_TRY(cudaMemsetAsync(c.detect_state, 0, (size_t)c.detect_tiles * 8, s));
-  if (segmented) PS_TRY(launch_check_offsets(c));
-  PS_TRY(kl->detect(c));
-  PS_TRY(launch_meta_stages(c));
+  const uint64_t eb = (uint64_t)c.key_bytes + (c.has_vals ? 4u : 0u);  // bytes per element
+  {
+    StageTimer t(0, s);
+    if (segmented) PS_TRY(launch_check_offsets(c));
+    PS_TRY(kl->detect(c));
+    t.done((uint64_t)n * c.key_bytes, segmented ? 2 : 1);
+  }
+  {
+    StageTimer t(1, s);
+    PS_TRY(launch_meta_stages(c));
+    t.done(0, 8);
+  }
   if (an && an->stats) {
     PS_TRY(cudaMemsetAsync(c.d_entropy, 0, sizeof(double), s));
     PS_TRY(launch_entropy(c, c.d_entropy));
+    g_launches += 1;
   }
   PlanHeader h;
   PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
@@ -226,13 +276,31 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     return PS_OK;
   }
 
-  PS_TRY(kl->small(c, h.n_small));
-  PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), (uint32_t)(h.leaf_ctr & 0xffffffffull)));
+  if (h.n_small) {
+    StageTimer t(2, s);
+    PS_TRY(kl->small(c, h.n_small));
+    t.done(2 * h.small_elems * eb, 1);
+  }
+  const uint32_t leaf_tiles = (uint32_t)(h.leaf_ctr & 0xffffffffull);
+  if (leaf_tiles) {
+    StageTimer t(3, s);
+    PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), leaf_tiles));
+    t.done(2 * h.place_elems * eb, 1);
+  }
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
     if ((int64_t)tiles > c.tiles_cap || (int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
-    PS_TRY(kl->level(c, d, items, tiles));
+    {
+      StageTimer t(4, s);
+      PS_TRY(kl->corank(c, d, items, tiles));
+      t.done(0, 1);
+    }
+    {
+      StageTimer t(5, s);
+      PS_TRY(kl->merge(c, d, tiles));
+      t.done(2 * h.level_elems[d] * eb, 1);
+    }
   }
   return PS_OK;
 }
@@ -396,6 +464,92 @@ ps_status ps_stream_status(void* stream) {
   }
   return PS_OK;
 }
+
+ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                       uint32_t* vals_out, int64_t n, void* stream) {
+  if (!launch_for(key_type) || n < 0) return PS_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n > 0 && (!keys_in || !keys_out)) return PS_ERR_INVALID_ARG;
+  if ((vals_in == nullptr) != (vals_out == nullptr)) return PS_ERR_INVALID_ARG;
+  const size_t kb = (size_t)key_bytes(key_type);
+  if (n <= 1) {
+    if (n == 1) {
+      std::memmove(keys_out, keys_in, kb);
+      if (vals_in) std::memmove(vals_out, vals_in, 4);
+    }
+    return PS_OK;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return PS_ERR_CUDA;
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals_in ? up((size_t)n * 4 + 16) : 0;
+  Ctx tmp;
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals_in != nullptr, n, false);
+  uint8_t* base = nullptr;
+  if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
+    return PS_ERR_OUT_OF_MEMORY;
+  void* dk = base;
+  uint32_t* dv = vals_in ? (uint32_t*)(base + kbytes) : nullptr;
+  void* ws = base + kbytes + vbytes;
+  ps_status st = PS_OK;
+  cudaError_t e = cudaMemcpyAsync(dk, keys_in, (size_t)n * kb, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && dv) e = cudaMemcpyAsync(dv, vals_in, (size_t)n * 4, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) st = cuda_status(e);
+  if (st == PS_OK) st = run(key_type, dk, dv, n, nullptr, 1, false, ws, wbytes, s, nullptr);
+  if (st == PS_OK) {
+    e = cudaMemcpyAsync(keys_out, dk, (size_t)n * kb, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && dv) e = cudaMemcpyAsync(vals_out, dv, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) st = cuda_status(e);
+  }
+  cudaFreeAsync(base, s);
+  e = cudaStreamSynchronize(s);
+  if (st == PS_OK && e != cudaSuccess) st = PS_ERR_CUDA;
+  return st;
+}
+
+ps_status ps_profile_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& p : g_prof_pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_prof_pending.clear();
+  for (int i = 0; i < kStages; ++i) {
+    g_prof_ms[i] = 0;
+    g_prof_launch[i] = 0;
+    g_prof_bytes[i] = 0;
+  }
+  g_prof_on = on ? 1 : 0;
+  return PS_OK;
+}
+
+ps_status ps_profile_read(ps_profile* out) {
+  if (!out) return PS_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  ps_status st = PS_OK;
+  for (auto& p : g_prof_pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess)
+      st = PS_ERR_CUDA;
+    g_prof_ms[p.stage] += ms;
+    g_prof_launch[p.stage] += p.launches;
+    g_prof_bytes[p.stage] += p.bytes;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  g_prof_pending.clear();
+  for (int i = 0; i < kStages; ++i) {
+    out->ms[i] = g_prof_ms[i];
+    out->launches[i] = g_prof_launch[i];
+    out->bytes[i] = g_prof_bytes[i];
+  }
+  return st;
+}
+
+uint64_t ps_launch_count(void) { return g_launches.load(); }
 
 const char* ps_status_string(ps_status status) {
   switch (status) {

@@ -83,6 +83,10 @@ struct PlanHeader {
   uint32_t pad0;
   unsigned long long leaf_ctr;               // (count << 32) | tiles of large-leaf placement
   unsigned long long level_ctr[kMaxLevels];  // per depth: (count << 32) | merge tiles
+  // element counts for the algorithmic-traffic accounting of stage 4
+  unsigned long long small_elems;            // elements of all subtree-in-SMEM tasks
+  unsigned long long place_elems;            // elements moved by large-leaf placement
+  unsigned long long level_elems[kMaxLevels];  // outputs of the merges of each depth pass
 };
 
 // One merge tile of a level pass: output [g0, next tile's g0 or hi) of the merge of

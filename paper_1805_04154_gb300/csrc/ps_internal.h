@@ -57,7 +57,8 @@ struct KeyLaunch {
   cudaError_t (*detect)(const Ctx&);
   cudaError_t (*small)(const Ctx&, uint32_t ntasks);
   cudaError_t (*place)(const Ctx&, uint32_t nitems, uint32_t ntiles);
-  cudaError_t (*level)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
+  cudaError_t (*corank)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
+  cudaError_t (*merge)(const Ctx&, int depth, uint32_t ntiles);
 };
 extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
 

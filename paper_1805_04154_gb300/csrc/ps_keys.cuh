@@ -68,7 +68,7 @@ struct Launch {
     return cudaGetLastError();
   }
 
-  static cudaError_t level(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
+  static cudaError_t corank(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
     if (ntiles == 0) return cudaSuccess;
     const int src = (depth + 1) & 1;
     const size_t off = (size_t)depth * c.level_cap;
@@ -76,12 +76,15 @@ struct Launch {
     corank_kernel<K><<<(ntiles + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, c.stream>>>(
         (const T*)c.k[src], c.S, c.nodeL, c.nodeR, c.level_items + off, c.level_tile_off + off, nitems, ntiles,
         c.tiles);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+  }
+
+  static cudaError_t merge(const Ctx& c, int depth, uint32_t ntiles) {
+    if (ntiles == 0) return cudaSuccess;
     return c.has_vals ? merge_v<true>(c, depth, ntiles) : merge_v<false>(c, depth, ntiles);
   }
 
-  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &level}; }
+  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &corank, &merge}; }
 };
 
 }  // namespace ps

@@ -227,6 +227,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
           if (slot < (uint32_t)small_cap) small_tasks[slot] = ~x;  // leaf task
           else post_status(&hdr->status, nullptr, kDevInternal);
+          atomicAdd(&hdr->small_elems, (unsigned long long)len);
         }
       } else {
         const bool desc = run_desc[x] != 0;
@@ -239,6 +240,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           if (slot < (uint32_t)level_cap) {
             leaf_items[slot] = x;
             leaf_tile_off[slot] = (uint32_t)(old & 0xffffffffu);
+            atomicAdd(&hdr->place_elems, (unsigned long long)((d & 1) ? len : 2 * (len / 2)));
           } else {
             post_status(&hdr->status, nullptr, kDevInternal);
           }
@@ -255,6 +257,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
           if (slot < (uint32_t)small_cap) small_tasks[slot] = x;
           else post_status(&hdr->status, nullptr, kDevInternal);
+          atomicAdd(&hdr->small_elems, (unsigned long long)size);
         }
       } else {
         const int d = ndepth[x];
@@ -267,6 +270,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           if (slot < (uint32_t)level_cap) {
             level_items[(size_t)d * level_cap + slot] = x;
             level_tile_off[(size_t)d * level_cap + slot] = (uint32_t)(old & 0xffffffffu);
+            atomicAdd(&hdr->level_elems[d], (unsigned long long)size);
           } else {
             post_status(&hdr->status, nullptr, kDevInternal);
           }
