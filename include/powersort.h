@@ -158,6 +158,25 @@ ps_status ps_profile_read(ps_profile* out);
 /* Number of kernels the library has launched in this process (all devices, all calls). */
 uint64_t ps_launch_count(void);
 
+/* Allocation-free sort of a small device array.  The paper has no counterpart; this is an
+ * integration entry point for callers that must not allocate device memory while they run
+ * (cudaMalloc / cudaFree can synchronize the whole device and can fail once a fixed memory
+ * budget is used up, and hosts that own all device memory through their own allocator forbid
+ * stray allocations).  Same semantics as ps_sort (stable in-place sort of keys[0..n) with
+ * optional vals, powersort merge order), but every piece of scratch memory lives in one
+ * fixed array inside the library's device image (about 9 MiB, held by every GPU that loads the
+ * library until the process exits), so the call never allocates.
+ *   - n <= PS_NOALLOC_MAX_N elements; larger n returns PS_ERR_INVALID_ARG and touches nothing.
+ *   - The first call on a device looks up the array's device address with that device current
+ *     (a one-time set-up per device); make that first call before any stream capture.
+ *   - All calls share the one array, which keeps the last call's contents (each call clears
+ *     what must start at zero).  Calls that overlap on the GPU -- on different streams or from
+ *     different host threads -- race on it and corrupt each other: serialize them.
+ *   - Synchronizes the stream before returning and reports device-posted errors itself.
+ * Other errors as for ps_sort_ws. */
+#define PS_NOALLOC_MAX_N 262144
+ps_status ps_sort_noalloc(int key_type, void* keys, uint32_t* vals, int64_t n, void* stream);
+
 /* Synchronizes `stream`, then reports (and clears) errors the device posted on the current
  * device since the last call: PS_ERR_TIMEOUT if a bounded wait gave up, PS_ERR_CUDA if the
  * stream itself failed, else PS_OK. */

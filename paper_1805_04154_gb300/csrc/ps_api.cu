@@ -567,3 +567,105 @@ const char* ps_status_string(ps_status status) {
 int ps_version(void) { return 100; }
 
 }  // extern "C"
+
+// =============================================================================================
+// Allocation-free entry point (ps_sort_noalloc).
+//
+// Some callers cannot allocate device memory while they run: cudaMalloc / cudaFree may
+// synchronize the whole device (stalling every other stream of a latency-critical loop), an
+// allocation can fail once a fixed memory budget has been handed out, and hosts that manage all
+// device memory through their own allocator (inference servers, plugins inside another
+// framework) forbid stray allocations.  For them this entry point sorts small arrays with all
+// of its scratch in one fixed array of device memory that lives in the library's module image:
+// every GPU that loads the library holds it (kNoAllocScratchBytes, about 9 MiB) until the
+// process exits.  Nothing here calls cudaMalloc, cudaFree or an allocating library routine.
+//
+// All calls share that array and it keeps whatever the last call left in it; every part that
+// must start at zero is cleared on the stream at the start of each call.  Calls whose work
+// overlaps on the GPU (different streams, or different host threads) race on the array and
+// corrupt each other's results: serialize them.
+// =============================================================================================
+static constexpr size_t kNoAllocScratchBytes = (size_t)9 << 20;
+static __device__ __align__(256) unsigned char ps_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+uint8_t* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of ps_noalloc_scratch on the current device.  The symbol name in host code
+// is only a host-side stand-in, so the address is looked up once per device, with that device
+// current, and cached.
+uint8_t* noalloc_scratch(int dev) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (dev < 0 || dev >= kMaxDevices) return nullptr;
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, ps_noalloc_scratch) != cudaSuccess || p == nullptr) return nullptr;
+    g_noalloc_addr[dev] = (uint8_t*)p;
+  }
+  return g_noalloc_addr[dev];
+}
+
+ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_t s) {
+  ps_status st = check_args(kt, keys, vals, n);
+  if (st != PS_OK) return st;
+  if (n > PS_NOALLOC_MAX_N) return PS_ERR_INVALID_ARG;
+  if (n <= 1) return PS_OK;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  uint8_t* scratch = noalloc_scratch(dev);
+  if (!scratch) return PS_ERR_CUDA;
+  Ctx c;
+  const size_t need = carve(c, scratch, kt, vals != nullptr, n, false);
+  if (need + 256 > kNoAllocScratchBytes) return PS_ERR_INTERNAL;
+  c.stream = s;
+  c.kt = kt;
+  c.key_bytes = key_bytes(kt);
+  c.has_vals = vals != nullptr;
+  c.n = (int32_t)n;
+  c.offsets = nullptr;
+  c.count = 1;
+  c.k[0] = keys;
+  c.v[0] = vals;
+  c.lib_status = (uint32_t*)(scratch + kNoAllocScratchBytes - 256);  // this entry's own status word
+  const KeyLaunch* kl = launch_for(kt);
+
+  PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
+  PS_TRY(cudaMemsetAsync(c.detect_state, 0, (size_t)c.detect_tiles * 8, s));
+  PS_TRY(cudaMemsetAsync(c.lib_status, 0, 4, s));
+  PS_TRY(kl->detect(c));
+  PS_TRY(launch_meta_stages(c));
+  g_launches += 9;
+  PlanHeader h;
+  PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
+  PS_TRY(cudaStreamSynchronize(s));
+  if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
+  if (h.status & kDevInternal) return PS_ERR_INTERNAL;
+  if (h.runs < 1 || h.runs > n) return PS_ERR_INTERNAL;
+  PS_TRY(kl->small(c, h.n_small));
+  PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), (uint32_t)(h.leaf_ctr & 0xffffffffull)));
+  g_launches += (h.n_small ? 1 : 0) + ((h.leaf_ctr & 0xffffffffull) ? 1 : 0);
+  for (int d = kMaxLevels - 1; d >= 0; --d) {
+    const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
+    if (tiles == 0) continue;
+    if ((int64_t)tiles > c.tiles_cap || (int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
+    PS_TRY(kl->corank(c, d, items, tiles));
+    PS_TRY(kl->merge(c, d, tiles));
+    g_launches += 2;
+  }
+  // device-posted errors of the merge stage come back synchronously: this entry point has no
+  // library status word to defer them to
+  uint32_t dev_status = 0;
+  PS_TRY(cudaMemcpyAsync(&dev_status, c.lib_status, 4, cudaMemcpyDeviceToHost, s));
+  PS_TRY(cudaStreamSynchronize(s));
+  if (dev_status & kDevTimeout) return PS_ERR_TIMEOUT;
+  if (dev_status) return PS_ERR_INTERNAL;
+  return PS_OK;
+}
+
+}  // namespace
+
+extern "C" ps_status ps_sort_noalloc(int key_type, void* keys, uint32_t* vals, int64_t n, void* stream) {
+  return run_noalloc(key_type, keys, vals, n, (cudaStream_t)stream);
+}
