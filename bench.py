@@ -265,7 +265,7 @@ def run_gpu(args):
     value = ws * n * args.steps / (total_ms / 1000.0) / 1e9
 
     peak, peak_kind = _peaks()
-    mt = prof["merge_tile"]
+    mt = prof["level_pass"]
     achieved = (mt["bytes"] / (mt["ms"] / 1000.0) / 1e9) if mt["ms"] > 0 else None
     traffic = None
     tpath = os.path.join(ROOT, "profiles", "merge_tile_traffic.json")
@@ -280,7 +280,7 @@ def run_gpu(args):
                 traffic = tr["dram_bytes_per_output_elem"] * elems_per_launch
         except Exception:
             traffic = None
-    roofline = {"bound": "hbm", "kernel": "merge_tile_kernel", "achieved": achieved, "peak": peak,
+    roofline = {"bound": "hbm", "kernel": "level_pass_kernel", "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                 "peak_kind": peak_kind,
                 "launches": mt["launches"], "ms_total": mt["ms"], "algorithmic_bytes_total": mt["bytes"]}

@@ -142,7 +142,7 @@ ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_i
 
 /* Measurement.  While enabled, every sort records CUDA events on its stream around its stages
  * (0 run detection, 1 node powers + merge tree + plan, 2 subtrees merged in shared memory,
- * 3 large-leaf placement, 4 co-rank search, 5 merge tiles of the level passes).
+ * 3 large-leaf placement, 4 unused, 5 level passes of the large merges).
  * ps_profile_read waits for the recorded events and returns, per stage since the last enable,
  * the device milliseconds, kernel launches and algorithmic HBM bytes (every element a stage
  * moves counted once read and once written: 2 x elements x (key bytes + payload bytes); run

@@ -24,7 +24,7 @@ __all__ = [
     "ps_launch_count", "STAGES",
 ]
 
-STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "corank", "merge_tile"]
+STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
 
 PS_KEY_I32, PS_KEY_U32, PS_KEY_U64, PS_KEY_F32 = 0, 1, 2, 3
 _STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_OUT_OF_MEMORY",

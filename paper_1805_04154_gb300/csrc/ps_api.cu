@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -52,7 +53,7 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.ndepth = (uint8_t*)take(N);
   c.ldepth = (uint8_t*)take(N);
   c.detect_tiles = (int32_t)((n + kDetectTile - 1) / kDetectTile);
-  c.detect_state = (uint64_t*)take((size_t)std::max<int32_t>(c.detect_tiles, 1) * 8);
+  c.detect_state = (uint64_t*)take((size_t)std::max<int32_t>(c.detect_tiles, 1) * 16);  // functions + prefixes
   const size_t tree_tiles = (size_t)(n + 1) / kTreeTile + 1;
   c.tree_sum = (int32_t*)take(tree_tiles * 32 * 4);
   c.tree_pre = (int32_t*)take(tree_tiles * 32 * 4);
@@ -62,10 +63,8 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.leaf_items = (int32_t*)take(cap * 4);
   c.leaf_tile_off = (uint32_t*)take(cap * 4);
   c.level_cap = (int32_t)cap;
-  c.level_items = (int32_t*)take((size_t)kMaxLevels * cap * 4);
+  c.level_items = (int4*)take((size_t)kMaxLevels * cap * sizeof(int4));
   c.level_tile_off = (uint32_t*)take((size_t)kMaxLevels * cap * 4);
-  c.tiles_cap = (int32_t)((size_t)n / kMergeTile + 2 * cap + 2);
-  c.tiles = (TileDesc*)take((size_t)c.tiles_cap * sizeof(TileDesc));
   c.hdr = (PlanHeader*)take(sizeof(PlanHeader));
   c.d_entropy = (double*)take(sizeof(double));
   return (cur + 255) & ~(size_t)255;
@@ -110,7 +109,7 @@ cudaMemPool_t lib_pool(int dev) {
 // ---- measurement: per-stage device time (CUDA events on the caller's stream), launches,
 // algorithmic bytes --------------------------------------------------------------------------
 constexpr int kStages = 8;  // 0 detect, 1 powers+tree+plan, 2 SMEM subtrees, 3 leaf placement,
-                            // 4 co-rank search, 5 merge tiles
+                            // 4 (unused), 5 level passes
 std::atomic<int> g_prof_on{0};
 std::atomic<unsigned long long> g_launches{0};
 struct ProfRec {
@@ -160,6 +159,17 @@ struct AnalyzeOut {
 };
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// Level-pass ring depth: PS_PASS_STAGES (2, 3, 4 or 6) overrides the default for tuning runs.
+int pass_stages_setting() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("PS_PASS_STAGES");
+    int x = e ? std::atoi(e) : 0;
+    v = (x == 2 || x == 3 || x == 4 || x == 6) ? x : 2;
+  }
+  return v;
+}
 
 ps_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return PS_OK;
@@ -215,16 +225,16 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
+  c.pass_stages = pass_stages_setting();
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
-  PS_TRY(cudaMemsetAsync(c.detect_state, 0, (size_t)c.detect_tiles * 8, s));
   const uint64_t eb = (uint64_t)c.key_bytes + (c.has_vals ? 4u : 0u);  // bytes per element
   {
     StageTimer t(0, s);
     if (segmented) PS_TRY(launch_check_offsets(c));
     PS_TRY(kl->detect(c));
-    t.done((uint64_t)n * c.key_bytes, segmented ? 2 : 1);
+    t.done(2 * (uint64_t)n * c.key_bytes, segmented ? 4 : 3);
   }
   {
     StageTimer t(1, s);
@@ -290,15 +300,10 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
-    if ((int64_t)tiles > c.tiles_cap || (int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
-    {
-      StageTimer t(4, s);
-      PS_TRY(kl->corank(c, d, items, tiles));
-      t.done(0, 1);
-    }
+    if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
     {
       StageTimer t(5, s);
-      PS_TRY(kl->merge(c, d, tiles));
+      PS_TRY(kl->merge(c, d, items, tiles));
       t.done(2 * h.level_elems[d] * eb, 1);
     }
   }
@@ -632,11 +637,10 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
-  PS_TRY(cudaMemsetAsync(c.detect_state, 0, (size_t)c.detect_tiles * 8, s));
   PS_TRY(cudaMemsetAsync(c.lib_status, 0, 4, s));
   PS_TRY(kl->detect(c));
   PS_TRY(launch_meta_stages(c));
-  g_launches += 9;
+  g_launches += 11;
   PlanHeader h;
   PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
   PS_TRY(cudaStreamSynchronize(s));
@@ -649,10 +653,9 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
-    if ((int64_t)tiles > c.tiles_cap || (int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
-    PS_TRY(kl->corank(c, d, items, tiles));
-    PS_TRY(kl->merge(c, d, tiles));
-    g_launches += 2;
+    if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
+    PS_TRY(kl->merge(c, d, items, tiles));
+    g_launches += 1;
   }
   // device-posted errors of the merge stage come back synchronously: this entry point has no
   // library status word to defer them to

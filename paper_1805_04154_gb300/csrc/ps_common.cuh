@@ -16,8 +16,8 @@ constexpr int kMaxLevels = 32;  // powers and depths are < 32
 
 // Stage 1 (run detection): one CTA scans a tile of kDetectTile positions.
 constexpr int kDetectThreads = 256;
-constexpr int kDetectItems = 16;
-constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 4096
+constexpr int kDetectItems = 32;
+constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 8192
 
 // Stage 3 (nearest-smaller-value tree): 8 warps x 32 rounds x 32 boundaries per tile.
 constexpr int kTreeWarps = 8;
@@ -26,8 +26,8 @@ constexpr int kTreeTile = kTreeWarps * kTreeRounds * 32;  // 8192
 
 // Stage 4 (merge passes over HBM): one CTA produces kMergeTile outputs of one merge.
 constexpr int kMergeThreads = 256;
-constexpr int kMergeItems = 16;
-constexpr int kMergeTile = kMergeThreads * kMergeItems;  // 4096
+constexpr int kMergeItems = 12;
+constexpr int kMergeTile = kMergeThreads * kMergeItems;  // 3072
 
 // Stage 4 (whole small subtrees in shared memory): a tree node whose range holds at most
 // sub_tile(key size) elements is merged completely inside one CTA.
@@ -39,20 +39,24 @@ __host__ __device__ constexpr int sub_tile(int key_bytes) { return key_bytes == 
 // integer: int32 flips the sign bit; float32 uses IEEE totalOrder (negative patterns are
 // complemented, non-negative ones get the sign bit set); unsigned types are themselves.
 // ---------------------------------------------------------------------------------------
+// le(a, b) is a <= b in the key order, written directly where a native compare exists.
 struct KeyI32 {
   typedef uint32_t T;
   static constexpr int kType = 0;
   __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x ^ 0x80000000u; }
+  __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return (int32_t)a <= (int32_t)b; }
 };
 struct KeyU32 {
   typedef uint32_t T;
   static constexpr int kType = 1;
   __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x; }
+  __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return a <= b; }
 };
 struct KeyU64 {
   typedef uint64_t T;
   static constexpr int kType = 2;
   __device__ __forceinline__ static uint64_t ord(uint64_t x) { return x; }
+  __device__ __forceinline__ static bool le(uint64_t a, uint64_t b) { return a <= b; }
 };
 struct KeyF32 {
   typedef uint32_t T;
@@ -60,6 +64,7 @@ struct KeyF32 {
   __device__ __forceinline__ static uint32_t ord(uint32_t x) {
     return x ^ ((uint32_t)((int32_t)x >> 31) | 0x80000000u);
   }
+  __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return ord(a) <= ord(b); }
 };
 
 // ---------------------------------------------------------------------------------------
@@ -76,7 +81,7 @@ enum DevStatus : uint32_t {
 struct PlanHeader {
   int32_t runs;             // r: number of detected runs (all segments)
   uint32_t status;          // DevStatus bits
-  uint32_t detect_ticket;   // dynamic tile counter of the detection scan
+  uint32_t pad1;
   int32_t max_leaf_depth;
   unsigned long long cost;  // merge cost M = sum of leaf depth x run length
   uint32_t n_small;         // subtree-in-SMEM tasks
@@ -87,12 +92,6 @@ struct PlanHeader {
   unsigned long long small_elems;            // elements of all subtree-in-SMEM tasks
   unsigned long long place_elems;            // elements moved by large-leaf placement
   unsigned long long level_elems[kMaxLevels];  // outputs of the merges of each depth pass
-};
-
-// One merge tile of a level pass: output [g0, next tile's g0 or hi) of the merge of
-// [lo, mid) and [mid, hi); i0 = elements taken from the left run before g0.
-struct TileDesc {
-  int32_t lo, mid, hi, g0, i0, pad[3];
 };
 
 // ---------------------------------------------------------------------------------------
@@ -110,6 +109,9 @@ __device__ __forceinline__ void fence_mbar_init() {
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;

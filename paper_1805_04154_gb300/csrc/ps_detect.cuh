@@ -8,8 +8,9 @@
 // p starts a run exactly when the automaton is in START at p (a segment start forces START).  The
 // transition functions compose associatively, so the state at every position is an exclusive
 // scan of them; attaching to each function the number of run starts it produces (which depends on
-// the entry state) makes the same scan count the runs, so run starts are written compacted in one
-// pass.  Cross-tile carries use decoupled look-back with bounded waits.
+// the entry state) makes the same scan count the runs, so run starts are written compacted.  The
+// scan runs as reduce (tile functions) -> one-CTA scan over tiles -> emit, reading the keys twice;
+// no block waits on another.
 #pragma once
 
 #include "ps_common.cuh"
@@ -52,38 +53,14 @@ __device__ __forceinline__ Fn fn_shfl_up(const Fn& f, int d) {
   r.c2 = __shfl_up_sync(0xffffffffu, f.c2, d);
   return r;
 }
-__device__ __forceinline__ Fn fn_shfl_down(const Fn& f, int d) {
-  Fn r;
-  r.map = __shfl_down_sync(0xffffffffu, f.map, d);
-  r.c0 = __shfl_down_sync(0xffffffffu, f.c0, d);
-  r.c1 = __shfl_down_sync(0xffffffffu, f.c1, d);
-  r.c2 = __shfl_down_sync(0xffffffffu, f.c2, d);
-  return r;
-}
 
-// Tile descriptor word for the look-back: [63:62] flag (1 aggregate, 2 inclusive prefix).
-// Aggregate: map in [5:0], c0/c1/c2 in 16-bit fields at 8, 24, 40 (tile counts <= 4096).
-// Prefix: exit state in [1:0], inclusive run count in [33:2].
-constexpr uint64_t kFlagAgg = 1ull << 62, kFlagPrefix = 2ull << 62, kFlagMask = 3ull << 62;
-
+// Tile function word: map in [5:0], c0/c1/c2 in 16-bit fields at 8, 24, 40 (tile counts <= 4096).
 __device__ __forceinline__ uint64_t pack_agg(const Fn& f) {
-  return kFlagAgg | (uint64_t)f.map | ((uint64_t)f.c0 << 8) | ((uint64_t)f.c1 << 24) | ((uint64_t)f.c2 << 40);
+  return (uint64_t)f.map | ((uint64_t)f.c0 << 8) | ((uint64_t)f.c1 << 24) | ((uint64_t)f.c2 << 40);
 }
 __device__ __forceinline__ Fn unpack_agg(uint64_t w) {
   return Fn{(uint32_t)(w & 63u), (uint32_t)((w >> 8) & 0xffffu), (uint32_t)((w >> 24) & 0xffffu),
             (uint32_t)((w >> 40) & 0xffffu)};
-}
-__device__ __forceinline__ uint64_t pack_prefix(uint32_t state, uint32_t count) {
-  return kFlagPrefix | (uint64_t)state | ((uint64_t)count << 2);
-}
-
-__device__ __forceinline__ void store_release_u64(uint64_t* p, uint64_t v) {
-  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ uint64_t load_acquire_u64(const uint64_t* p) {
-  uint64_t v;
-  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
 }
 
 // Largest k with offsets[k] <= p (the segment containing p when segments are non-empty).
@@ -96,60 +73,188 @@ __device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t co
   return lo;
 }
 
-// One CTA per tile, tiles taken in order from a ticket counter (so predecessors have started).
-// Outputs: run starts S[0..r-1] (S[r] = n written by the last tile), run_desc[k], run_seg[k],
-// hdr->runs = r.
+// The thread's view of its kDetectItems = 32 consecutive positions p0 .. p0+31:
+//   L  bit q (q = 0..32): key[p0+q-1] <= key[p0+q]  (the pair into position p0+q)
+//   F  bit q (q = 0..32): position p0+q is forced to START (position 0 or a segment start)
+// Runs are walked start to start with bit operations instead of one automaton step per position:
+// a run that starts at position s has direction L[s+1] (weakly ascending if set) and the next
+// run starts at the first q >= s+2 whose pair disagrees with that direction, or at the first
+// forced q >= s+1.  A run already open when the thread begins, with direction e, ends at the
+// first q >= 0 whose pair disagrees with e (or is forced); entering in START at position p0-1
+// behaves like entering with direction L[0].
 template <class K>
-__global__ void __launch_bounds__(kDetectThreads)
-detect_runs_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
-                   int32_t count, int32_t* __restrict__ S, uint8_t* __restrict__ run_desc,
-                   int32_t* __restrict__ run_seg, uint64_t* __restrict__ tile_state, PlanHeader* hdr,
-                   uint32_t* lib_status) {
+struct ThreadRuns {
   typedef typename K::T T;
-  __shared__ T sk[kDetectTile + 2];
-  __shared__ Fn warp_tot[kDetectThreads / 32];
-  __shared__ uint32_t s_tile, s_entry, s_base;
+  int32_t p0, nvalid;  // positions p0 .. p0+nvalid-1 exist
+  uint64_t L, F, valid;
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(&hdr->detect_ticket, 1u);
-  __syncthreads();
-  const int32_t tile = (int32_t)s_tile;
-  const int32_t t0 = tile * kDetectTile;
-
-  // keys [t0-1, t0+kDetectTile] into shared memory (coalesced)
-  for (int i = tid; i < kDetectTile + 2; i += kDetectThreads) {
-    const int64_t g = (int64_t)t0 - 1 + i;
-    if (g >= 0 && g < n) sk[i] = keys[g];
-  }
-  __syncthreads();
-
-  // this thread's positions p in [p0, p1); seg0 = segment holding p0, nxt0 = the first segment
-  // start >= p0 (a position is a segment start iff it equals some offsets[k])
-  const int32_t p0 = t0 + tid * kDetectItems;
-  const int32_t p1 = min(p0 + kDetectItems, n);
-  int32_t seg0 = 0, nxt0 = n;
-  if (offsets != nullptr && p0 < n) {
-    seg0 = segment_of(offsets, count, p0);
-    nxt0 = ((int32_t)offsets[seg0] == p0) ? p0 : (int32_t)offsets[seg0 + 1];
-  }
-  // transition kind into position p: 2 = forced start (p = 0 or a segment start), else the pair
-  auto kind_at = [&](int32_t p, bool seg_start) -> uint32_t {
-    if (p == 0 || seg_start) return 2u;
-    return K::ord(sk[p - t0]) <= K::ord(sk[p - t0 + 1]) ? 0u : 1u;
-  };
-
-  // thread aggregate
-  Fn agg = fn_identity();
-  {
-    int32_t nxt = nxt0;
-    for (int32_t p = p0; p < p1; ++p) {
-      const bool st = (p == nxt);
-      if (st) nxt = (int32_t)offsets[segment_of(offsets, count, p) + 1];
-      agg = fn_then(agg, fn_of_kind(kind_at(p, st)));
+  __device__ __forceinline__ void load(const T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+                                       int32_t count, int32_t tile, int tid) {
+    p0 = tile * kDetectTile + tid * kDetectItems;
+    nvalid = max(0, min(kDetectItems, n - p0));
+    valid = (nvalid >= 64) ? ~0ull : ((1ull << nvalid) - 1ull);
+    L = 0;
+    F = 0;
+    if (nvalid == 0) return;
+    T prev = (p0 > 0) ? keys[p0 - 1] : (T)0;
+    if (p0 + kDetectItems < n) {
+      constexpr int kPer = 16 / (int)sizeof(T);
+      const uint4* src = reinterpret_cast<const uint4*>(keys + p0);  // 128-byte aligned
+#pragma unroll
+      for (int v = 0; v < kDetectItems / kPer; ++v) {
+        const uint4 w = __ldg(src + v);
+        const T* wt = reinterpret_cast<const T*>(&w);
+#pragma unroll
+        for (int u = 0; u < kPer; ++u) {
+          const T cur = wt[u];
+          L |= (uint64_t)(K::ord(prev) <= K::ord(cur)) << (v * kPer + u);
+          prev = cur;
+        }
+      }
+      L |= (uint64_t)(K::ord(prev) <= K::ord(keys[p0 + kDetectItems])) << kDetectItems;
+    } else {
+      for (int q = 0; q < nvalid; ++q) {
+        const T cur = keys[p0 + q];
+        L |= (uint64_t)(K::ord(prev) <= K::ord(cur)) << q;
+        prev = cur;
+      }
+    }
+    if (p0 == 0) F |= 1ull;
+    if (offsets != nullptr) {
+      // every offsets value in [p0, p0 + kDetectItems] marks a forced start
+      int32_t k = segment_of(offsets, count, p0);
+      while (k <= count) {
+        const int64_t o = offsets[k];
+        if (o > (int64_t)p0 + kDetectItems) break;
+        if (o >= p0) F |= 1ull << (int)(o - p0);
+        ++k;
+      }
     }
   }
+  // first run start at or after position 0 for a run entered with direction e (1 = ascending)
+  __device__ __forceinline__ int first_start(uint32_t e) const {
+    const uint64_t c = (((e ? ~L : L)) | F) & valid;
+    return c ? __ffsll((long long)c) - 1 : 64;
+  }
+  // next run start after a run that starts at pos (pos < nvalid), or 64
+  __device__ __forceinline__ int next_start(int pos) const {
+    const uint32_t d = (uint32_t)(L >> (pos + 1)) & 1u;
+    const uint64_t ge2 = (pos + 2 >= 64) ? 0ull : (~0ull << (pos + 2));
+    const uint64_t ge1 = ~0ull << (pos + 1);
+    const uint64_t c = ((((d ? ~L : L)) & ge2) | (F & ge1)) & valid;
+    return c ? __ffsll((long long)c) - 1 : 64;
+  }
+  // state after the thread's last position for a chain whose last run starts at pos
+  __device__ __forceinline__ uint32_t open_state(int pos) const {
+    if (pos + 1 >= kDetectItems) return 0u;  // the last position itself starts a run
+    return ((L >> (pos + 1)) & 1ull) ? 1u : 2u;
+  }
+  // walk the chain from its first start; returns the number of starts and the exit state
+  __device__ __forceinline__ void chain(int pos, uint32_t none_state, uint32_t& cnt, uint32_t& exit_state) const {
+    cnt = 0;
+    exit_state = none_state;
+    while (pos < nvalid) {
+      ++cnt;
+      exit_state = open_state(pos);
+      pos = next_start(pos);
+    }
+  }
+  __device__ __forceinline__ Fn aggregate() const {
+    if (nvalid == 0) return fn_identity();
+    Fn f;
+    if (F & 1ull) {
+      uint32_t c, x;
+      chain(0, 0u, c, x);
+      f.map = x | (x << 2) | (x << 4);
+      f.c0 = f.c1 = f.c2 = c;
+      return f;
+    }
+    uint32_t c1, x1, c0, x0;
+    chain(first_start(1u), 1u, c1, x1);  // entered ascending
+    chain(first_start(0u), 2u, c0, x0);  // entered descending
+    const bool l0 = (L & 1ull) != 0;    // entering at START behaves like direction L[0]
+    f.map = (l0 ? x1 : x0) | (x1 << 2) | (x0 << 4);
+    f.c0 = l0 ? c1 : c0;
+    f.c1 = c1;
+    f.c2 = c0;
+    return f;
+  }
+};
 
-  // block exclusive scan of the thread aggregates
+// Pass 1: the composed transition function (with run-start counts) of every tile.
+template <class K>
+__global__ void __launch_bounds__(kDetectThreads)
+detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+                     int32_t count, uint64_t* __restrict__ tile_agg) {
+  __shared__ Fn warp_tot[kDetectThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  ThreadRuns<K> tr;
+  tr.load(keys, n, offsets, count, blockIdx.x, tid);
+  Fn incl = tr.aggregate();
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const Fn up = fn_shfl_up(incl, d);
+    if (lane >= d) incl = fn_then(up, incl);
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  __syncthreads();
+  if (tid == 0) {
+    Fn t = fn_identity();
+    for (int w = 0; w < kDetectThreads / 32; ++w) t = fn_then(t, warp_tot[w]);
+    tile_agg[blockIdx.x] = pack_agg(t);
+  }
+}
+
+// Pass 2 (one CTA of 1024 threads): scan of the tile functions from the START state at
+// position 0.  tile_pre[t] = (state entering tile t) | (run starts before tile t) << 2;
+// hdr->runs = r and S[r] = n.
+static __global__ void __launch_bounds__(1024)
+detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int32_t n, uint64_t* __restrict__ tile_pre,
+                   int32_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
+  __shared__ Fn warp_tot[32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t per = (ntiles + 1023) / 1024;
+  const int32_t t0 = tid * per, t1 = min(t0 + per, ntiles);
+  Fn mine = fn_identity();
+  for (int32_t t = t0; t < t1; ++t) mine = fn_then(mine, unpack_agg(tile_agg[t]));
+  Fn incl = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const Fn up = fn_shfl_up(incl, d);
+    if (lane >= d) incl = fn_then(up, incl);
+  }
+  if (lane == 31) warp_tot[warp] = incl;
+  Fn excl = fn_shfl_up(incl, 1);
+  if (lane == 0) excl = fn_identity();
+  __syncthreads();
+  Fn wp = fn_identity();
+  for (int w = 0; w < warp; ++w) wp = fn_then(wp, warp_tot[w]);
+  excl = fn_then(wp, excl);
+  uint32_t state = fn_exit(excl, 0), cnt = fn_cnt(excl, 0);
+  for (int32_t t = t0; t < t1; ++t) {
+    tile_pre[t] = (uint64_t)state | ((uint64_t)cnt << 2);
+    const Fn f = unpack_agg(tile_agg[t]);
+    cnt += fn_cnt(f, state);
+    state = fn_exit(f, state);
+  }
+  if (t0 < ntiles && t1 == ntiles) {
+    hdr->runs = (int32_t)cnt;
+    S[cnt] = n;
+  }
+}
+
+// Pass 3: every thread replays its positions from its entry state and writes its run starts
+// S[k], directions run_desc[k] and segments run_seg[k] at their global ranks.
+template <class K>
+__global__ void __launch_bounds__(kDetectThreads)
+detect_emit_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+                   int32_t count, const uint64_t* __restrict__ tile_pre, int32_t* __restrict__ S,
+                   uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
+  __shared__ Fn warp_tot[kDetectThreads / 32];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  ThreadRuns<K> tr;
+  tr.load(keys, n, offsets, count, blockIdx.x, tid);
+  const Fn agg = tr.aggregate();
   Fn incl = agg;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -160,101 +265,32 @@ detect_runs_kernel(const typename K::T* __restrict__ keys, int32_t n, const int6
   Fn excl = fn_shfl_up(incl, 1);
   if (lane == 0) excl = fn_identity();
   __syncthreads();
-  Fn warp_prefix = fn_identity();
-  for (int w = 0; w < warp; ++w) warp_prefix = fn_then(warp_prefix, warp_tot[w]);
-  excl = fn_then(warp_prefix, excl);
-
-  // tile aggregate and look-back (warp 0)
-  if (warp == 0) {
-    Fn tile_agg = fn_identity();
-    for (int w = 0; w < kDetectThreads / 32; ++w) tile_agg = fn_then(tile_agg, warp_tot[w]);
-    uint32_t entry = 0, base = 0;
-    if (tile == 0) {
-      if (lane == 0) store_release_u64(&tile_state[0], pack_prefix(fn_exit(tile_agg, 0), fn_cnt(tile_agg, 0)));
-    } else {
-      if (lane == 0) store_release_u64(&tile_state[tile], pack_agg(tile_agg));
-      Fn acc = fn_identity();  // composition of tiles (pos, tile)
-      int32_t pos = tile - 1;
-      bool done = false, timed_out = false;
-      uint32_t spins = 0;
-      while (!done) {
-        const int32_t q = pos - lane;
-        uint64_t w = (q >= 0) ? load_acquire_u64(&tile_state[q]) : kFlagPrefix;  // before tile 0: START, 0
-        // wait until every descriptor in the window is published
-        while (__any_sync(0xffffffffu, (w & kFlagMask) == 0)) {
-          if (++spins > kSpinLimit) { timed_out = true; break; }
-          __nanosleep(64);
-          if ((w & kFlagMask) == 0) w = load_acquire_u64(&tile_state[q]);
-        }
-        if (__any_sync(0xffffffffu, timed_out)) { timed_out = true; break; }
-        const uint32_t pmask = __ballot_sync(0xffffffffu, (w & kFlagMask) == kFlagPrefix);
-        const int first_prefix = pmask ? (__ffs(pmask) - 1) : 32;
-        // ordered product of the aggregates of lanes [0, first_prefix): higher lanes first
-        Fn v = (lane < first_prefix) ? unpack_agg(w) : fn_identity();
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-          const Fn hi = fn_shfl_down(v, d);
-          if (lane + d < 32) v = fn_then(hi, v);
-        }
-        // lane 0 holds product over lanes 31..0 (identity beyond first_prefix)
-        v.map = __shfl_sync(0xffffffffu, v.map, 0);
-        v.c0 = __shfl_sync(0xffffffffu, v.c0, 0);
-        v.c1 = __shfl_sync(0xffffffffu, v.c1, 0);
-        v.c2 = __shfl_sync(0xffffffffu, v.c2, 0);
-        acc = fn_then(v, acc);
-        if (pmask) {
-          const uint64_t pw = __shfl_sync(0xffffffffu, w, first_prefix);
-          const uint32_t st = (uint32_t)(pw & 3u);
-          const uint32_t cnt = (uint32_t)((pw >> 2) & 0xffffffffu);
-          entry = fn_exit(acc, st);
-          base = cnt + fn_cnt(acc, st);
-          done = true;
-        } else {
-          pos -= 32;
-        }
-      }
-      if (timed_out) {
-        if (lane == 0) post_status(&hdr->status, lib_status, kDevTimeout);
-        entry = 0;
-        base = 0;
-      }
-      if (lane == 0)
-        store_release_u64(&tile_state[tile],
-                          pack_prefix(fn_exit(tile_agg, entry), base + fn_cnt(tile_agg, entry)));
-    }
-    if (lane == 0) {
-      s_entry = entry;
-      s_base = base;
-    }
-  }
-  __syncthreads();
-  const uint32_t tile_entry = s_entry, tile_base = s_base;
-
-  // emit the run starts of this thread's positions
-  uint32_t state = fn_exit(excl, tile_entry);
+  Fn wp = fn_identity();
+  for (int w = 0; w < warp; ++w) wp = fn_then(wp, warp_tot[w]);
+  excl = fn_then(wp, excl);
+  if (tr.nvalid == 0) return;
+  const uint64_t pre = tile_pre[blockIdx.x];
+  const uint32_t tile_entry = (uint32_t)(pre & 3u), tile_base = (uint32_t)(pre >> 2);
+  const uint32_t entry = fn_exit(excl, tile_entry);  // state at position p0 - 1
   uint32_t idx = tile_base + fn_cnt(excl, tile_entry);
-  int32_t nxt = nxt0, cur_seg = seg0;
-  for (int32_t p = p0; p < p1; ++p) {
-    const bool st = (p == nxt);
-    if (st) {
-      cur_seg = segment_of(offsets, count, p);
-      nxt = (int32_t)offsets[cur_seg + 1];
-    }
-    state = fn_exit(fn_of_kind(kind_at(p, st)), state);
-    if (state == 0) {
-      // descending iff the pair (p, p+1) lies inside the segment and is strictly decreasing
-      bool desc = false;
-      if (p + 1 < n && p + 1 != nxt) desc = !(K::ord(sk[p + 1 - t0]) <= K::ord(sk[p + 2 - t0]));
+  int pos;
+  if (tr.F & 1ull) pos = 0;
+  else if (entry == 0) pos = tr.first_start((uint32_t)(tr.L & 1ull));
+  else pos = tr.first_start(entry == 1 ? 1u : 0u);
+  int32_t seg = 0;
+  if (offsets != nullptr) seg = segment_of(offsets, count, tr.p0);
+  while (pos < tr.nvalid) {
+    const int32_t p = tr.p0 + pos;
+    if (offsets != nullptr && ((tr.F >> pos) & 1ull)) seg = segment_of(offsets, count, p);
+    // descending iff the pair (p, p+1) lies inside the segment and is strictly decreasing
+    const bool desc = (p + 1 < n) && !((tr.F >> (pos + 1)) & 1ull) && !((tr.L >> (pos + 1)) & 1ull);
+    if (idx < (uint32_t)n) {  // always true when the tile counts are consistent
       S[idx] = p;
       run_desc[idx] = desc ? 1 : 0;
-      if (run_seg) run_seg[idx] = cur_seg;
-      ++idx;
+      if (run_seg) run_seg[idx] = seg;
     }
-  }
-  // the thread holding the last position closes the run array
-  if (p0 < n && p1 == n) {
-    S[idx] = n;
-    hdr->runs = (int32_t)idx;
+    ++idx;
+    pos = tr.next_start(pos);
   }
 }
 

@@ -38,14 +38,13 @@ struct Ctx {
   int32_t* tree_pre = nullptr;
 
   int32_t sub_lim = 0;          // subtree-in-SMEM element limit
+  int pass_stages = 2;          // shared-memory stages of the level-pass ring (2, 3, 4 or 6)
   int32_t* small_tasks = nullptr;
   int32_t* leaf_items = nullptr;
   uint32_t* leaf_tile_off = nullptr;
-  int32_t* level_items = nullptr;      // [kMaxLevels][level_cap]
+  int4* level_items = nullptr;         // [kMaxLevels][level_cap]: node (lo, mid, hi, boundary)
   uint32_t* level_tile_off = nullptr;
   int32_t level_cap = 0;
-  TileDesc* tiles = nullptr;
-  int32_t tiles_cap = 0;
 
   PlanHeader* hdr = nullptr;
   uint32_t* lib_status = nullptr;  // per-device status word owned by the library
@@ -57,8 +56,7 @@ struct KeyLaunch {
   cudaError_t (*detect)(const Ctx&);
   cudaError_t (*small)(const Ctx&, uint32_t ntasks);
   cudaError_t (*place)(const Ctx&, uint32_t nitems, uint32_t ntiles);
-  cudaError_t (*corank)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
-  cudaError_t (*merge)(const Ctx&, int depth, uint32_t ntiles);
+  cudaError_t (*merge)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
 };
 extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
 

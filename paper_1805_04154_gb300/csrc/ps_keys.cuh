@@ -2,6 +2,8 @@
 // ps_keys_*.cu translation units.
 #pragma once
 
+#include <algorithm>
+
 #include "ps_detect.cuh"
 #include "ps_internal.h"
 #include "ps_merge.cuh"
@@ -13,9 +15,12 @@ struct Launch {
   typedef typename K::T T;
 
   static cudaError_t detect(const Ctx& c) {
-    detect_runs_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
-        (const T*)c.k[0], c.n, c.offsets, c.count, c.S, c.run_desc, c.run_seg, c.detect_state, c.hdr,
-        c.lib_status);
+    detect_reduce_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>((const T*)c.k[0], c.n, c.offsets,
+                                                                              c.count, c.detect_state);
+    detect_scan_kernel<<<1, 1024, 0, c.stream>>>(c.detect_state, c.detect_tiles, c.n, c.detect_state + c.detect_tiles,
+                                                 c.S, c.hdr);
+    detect_emit_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
+        (const T*)c.k[0], c.n, c.offsets, c.count, c.detect_state + c.detect_tiles, c.S, c.run_desc, c.run_seg);
     return cudaGetLastError();
   }
 
@@ -52,39 +57,48 @@ struct Launch {
     return cudaGetLastError();
   }
 
-  template <bool V>
-  static cudaError_t merge_v(const Ctx& c, int depth, uint32_t ntiles) {
-    static bool attr = false;
-    const size_t bytes = MergeLayout<K, V>::kBytes;
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(merge_tile_kernel<K, V>,
+  template <bool V, int NS>
+  static cudaError_t merge_vs(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
+    static int blocks_per_sm = 0;
+    static int sms = 0;
+    const size_t bytes = PassLayout<K, V, NS>::kBytes;
+    if (blocks_per_sm == 0) {
+      cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<K, V, NS>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
-      attr = true;
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, level_pass_kernel<K, V, NS>, kPassThreads,
+                                                        bytes);
+      if (e != cudaSuccess) return e;
+      if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
     const int src = (depth + 1) & 1, dst = depth & 1;
-    merge_tile_kernel<K, V><<<ntiles, kMergeThreads, bytes, c.stream>>>(
-        (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.tiles, c.hdr, c.lib_status);
-    return cudaGetLastError();
-  }
-
-  static cudaError_t corank(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
-    if (ntiles == 0) return cudaSuccess;
-    const int src = (depth + 1) & 1;
     const size_t off = (size_t)depth * c.level_cap;
-    const uint32_t warps_per_block = 8;
-    corank_kernel<K><<<(ntiles + warps_per_block - 1) / warps_per_block, 32 * warps_per_block, 0, c.stream>>>(
-        (const T*)c.k[src], c.S, c.nodeL, c.nodeR, c.level_items + off, c.level_tile_off + off, nitems, ntiles,
-        c.tiles);
+    const uint32_t grid = (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
+    level_pass_kernel<K, V, NS><<<grid, kPassThreads, bytes, c.stream>>>(
+        (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.level_tile_off + off, nitems,
+        ntiles, c.hdr, c.lib_status);
     return cudaGetLastError();
   }
 
-  static cudaError_t merge(const Ctx& c, int depth, uint32_t ntiles) {
-    if (ntiles == 0) return cudaSuccess;
-    return c.has_vals ? merge_v<true>(c, depth, ntiles) : merge_v<false>(c, depth, ntiles);
+  template <bool V>
+  static cudaError_t merge_v(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
+    switch (c.pass_stages) {
+      case 3: return merge_vs<V, 3>(c, depth, nitems, ntiles);
+      case 4: return merge_vs<V, 4>(c, depth, nitems, ntiles);
+      case 6: return merge_vs<V, 6>(c, depth, nitems, ntiles);
+      default: return merge_vs<V, 2>(c, depth, nitems, ntiles);
+    }
   }
 
-  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &corank, &merge}; }
+  static cudaError_t merge(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
+    if (ntiles == 0) return cudaSuccess;
+    return c.has_vals ? merge_v<true>(c, depth, nitems, ntiles) : merge_v<false>(c, depth, nitems, ntiles);
+  }
+
+  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &merge}; }
 };
 
 }  // namespace ps

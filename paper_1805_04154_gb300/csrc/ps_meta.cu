@@ -200,7 +200,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
                             const int32_t* __restrict__ nodeR, const uint8_t* __restrict__ ndepth,
                             uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
-                            int32_t* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
+                            int4* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
                             int32_t level_cap, int32_t small_cap, PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   unsigned long long cost = 0;
@@ -268,7 +268,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
           if (slot < (uint32_t)level_cap) {
-            level_items[(size_t)d * level_cap + slot] = x;
+            level_items[(size_t)d * level_cap + slot] = make_int4(lo, S[x], hi, x);
             level_tile_off[(size_t)d * level_cap + slot] = (uint32_t)(old & 0xffffffffu);
             atomicAdd(&hdr->level_elems[d], (unsigned long long)size);
           } else {
