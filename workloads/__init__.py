@@ -36,7 +36,7 @@ def build(force: bool = False) -> str:
     """Compile gen.cpp into libpsgen.so (host code; portable C++17, no arch flags)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", _SRC, "-o", tmp])
+        subprocess.check_call(["g++", "-std=c++17", "-O2", "-shared", "-fPIC", "-pthread", _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB
 

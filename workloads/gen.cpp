@@ -10,7 +10,9 @@
 // All arithmetic is integer or IEEE double and gives identical streams on x86-64 and aarch64.
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -201,18 +203,31 @@ void psgen_segment_sizes(uint64_t seed, int64_t count, double lo_exp, double hi_
 }
 
 // Segmented inputs: segment k of the given sizes (offsets[k]..offsets[k+1]) is filled like
-// psgen_runs32 with max_len = floor(2 * sqrt(size)), each from its own stream.  vals[i] = i.
+// psgen_runs32 with max_len = floor(2 * sqrt(size)), each from its own stream (so the result
+// does not depend on how the segments are spread over threads).  vals[i] = i.
 void psgen_segmented_runs32(uint64_t seed, int64_t count, const int64_t* offsets, double desc_frac,
                             int is_signed, uint32_t* keys, uint32_t* vals) {
-  for (int64_t k = 0; k < count; ++k) {
-    const int64_t lo = offsets[k], len = offsets[k + 1] - offsets[k];
-    if (len <= 0) continue;
-    Rng g(seed * 0x9e3779b97f4a7c15ull + (uint64_t)k + 1);
-    int64_t max_len = (int64_t)std::floor(2.0 * std::sqrt((double)len));
-    runs32(g, len, max_len < 1 ? 1 : max_len, desc_frac, is_signed, keys + lo);
-  }
-  if (vals)
-    for (int64_t i = 0; i < offsets[count]; ++i) vals[i] = (uint32_t)i;
+  std::atomic<int64_t> next(0);
+  auto worker = [&]() {
+    for (;;) {
+      const int64_t k = next.fetch_add(1);
+      if (k >= count) break;
+      const int64_t lo = offsets[k], len = offsets[k + 1] - offsets[k];
+      if (len <= 0) continue;
+      Rng g(seed * 0x9e3779b97f4a7c15ull + (uint64_t)k + 1);
+      int64_t max_len = (int64_t)std::floor(2.0 * std::sqrt((double)len));
+      runs32(g, len, max_len < 1 ? 1 : max_len, desc_frac, is_signed, keys + lo);
+      if (vals)
+        for (int64_t i = lo; i < lo + len; ++i) vals[i] = (uint32_t)i;
+    }
+  };
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt == 0) nt = 1;
+  if (nt > 32) nt = 32;
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t + 1 < nt; ++t) th.emplace_back(worker);
+  worker();
+  for (auto& t : th) t.join();
 }
 
 }  // extern "C"
