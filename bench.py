@@ -125,6 +125,139 @@ def _cpu_baseline(keys, vals, sample_desc: str):
             "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
 
 
+def measure_batched(ps, dev, count: int, reps: int = 3):
+    """10,000 uneven int32 arrays (sizes floor(2^U(8,20)), runs uniform in [1, 2 sqrt(size)])
+    sorted in one segmented call vs one plain call per array, same device-resident inputs."""
+    import numpy as np
+    import torch
+    import workloads
+    keys, vals, off = workloads.segmented_i32(count, seed=SEED)
+    n = keys.size
+    k0 = torch.from_numpy(keys).to(dev)
+    v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
+    doff = torch.from_numpy(off).to(dev)
+    dk, dv = k0.clone(), v0.clone()
+    ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n, True), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    best = None
+    for rep in range(reps + 1):
+        dk.copy_(k0)
+        dv.copy_(v0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ps.ps_sort_segmented_ws(dk, dv, doff, ws, key_type=ps.PS_KEY_I32, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rep > 0:
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+    batched_ms = best
+    out_k, out_v = dk.clone(), dv.clone()
+    # one plain ps_sort_ws per array on the same data (workspace sized for the largest array)
+    dk.copy_(k0)
+    dv.copy_(v0)
+    sizes = np.diff(off)
+    wsp = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, int(sizes.max()), False), dtype=torch.uint8,
+                      device=dev)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for a, b in zip(off[:-1], off[1:]):
+        ps.ps_sort_ws(dk[a:b], dv[a:b], wsp, key_type=ps.PS_KEY_I32, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    plain_ms = e0.elapsed_time(e1)
+    identical = bool(torch.equal(out_k, dk)) and bool(torch.equal(out_v, dv))
+    del ws, wsp, k0, v0, out_k, out_v
+    return {"workload": f"{count} int32 arrays, sizes floor(2^U(8,20)), runs uniform in [1, 2*sqrt(size)], "
+                        "uint32 payload", "keys": int(n), "segments": count,
+            "batched_ms": batched_ms, "batched_gkeys_s": n / (batched_ms / 1e3) / 1e9,
+            "plain_loop_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
+            "speedup": plain_ms / batched_ms, "identical_results": identical,
+            "batched_entry": "ps_sort_segmented_ws (one call)",
+            "plain_entry": "ps_sort_ws per array"}
+
+
+def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
+    """Poisson arrivals of float32 sort requests (sizes floor(2^U(10,24)), ~1% NaN/+-0, Pareto(1.5)
+    runs, uint32 payload): continuous batching (SortServer, 64 GB budget) vs one request at a time
+    through ps_sort_host, both from pinned host memory to pinned host memory."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1805_04154_gb300.serve import SortServer, latency_stats
+    rng = np.random.default_rng(SEED)
+    reqs = []
+    for i in range(nreq):
+        m = int(2 ** rng.uniform(10, 24))
+        k, v = workloads.pareto_f32(m, seed=SEED * 7919 + i, alpha=1.5, special_frac=0.01)
+        reqs.append((torch.from_numpy(k.view(np.int32)).pin_memory(), torch.from_numpy(v.view(np.int32)).pin_memory()))
+    total = sum(k.numel() for k, _ in reqs)
+    outs = [(torch.empty_like(k, pin_memory=True), torch.empty_like(v, pin_memory=True)) for k, v in reqs]
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_one(i):
+        k, v = reqs[i]
+        ok, ov = outs[i]
+        ps.ps_sort_host_ptr(ps.PS_KEY_F32, k.data_ptr(), v.data_ptr(), ok.data_ptr(), ov.data_ptr(), k.numel(),
+                            stream=stream)
+
+    for i in range(min(3, nreq)):
+        plain_one(i)
+    t0 = time.perf_counter()
+    for i in range(nreq):
+        plain_one(i)
+    plain_busy = time.perf_counter() - t0
+    capacity = nreq / plain_busy  # requests per second of back-to-back plain launches
+    srv_cfg = dict(budget_bytes=64 << 30, max_batch_keys=1 << 25, slots=3)
+    warm = SortServer(ps.PS_KEY_F32, **srv_cfg)
+    for i in range(min(4, nreq)):
+        warm.submit(reqs[i][0], reqs[i][1], outs[i][0], outs[i][1])
+    warm.drain(120)
+    warm.close()
+    out = {"workload": f"{nreq} float32 requests, sizes floor(2^U(10,24)), ~1% NaN/+-0 (totalOrder), "
+                       "Pareto(1.5) runs, uint32 payload, Poisson arrivals", "keys": int(total),
+           "plain_capacity_req_s": capacity, "plain_back_to_back_gkeys_s": total / plain_busy / 1e9, "loads": {}}
+    for load in loads:
+        lam = load * capacity
+        gaps = rng.exponential(1.0 / lam, size=nreq)
+        arrivals = np.cumsum(gaps)
+        # continuous batching
+        srv = SortServer(ps.PS_KEY_F32, **srv_cfg)
+        handles = []
+        start = time.perf_counter()
+        for i in range(nreq):
+            wait = arrivals[i] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(wait)  # sleeping releases the GIL to the server's threads
+            h = srv.submit(reqs[i][0], reqs[i][1], outs[i][0], outs[i][1])
+            h.t_submit = start + arrivals[i]  # latency counts from the scheduled arrival
+            handles.append(h)
+        srv.drain(600)
+        srv.close()
+        sb = latency_stats(handles)
+        sb["batches"] = srv.batches
+        sb["server"] = {"slots": len(srv._free), "max_batch_keys": srv.cap, "held_bytes": srv.held_bytes}
+        # sequential plain launches on the same arrival trace
+        lat = []
+        start = time.perf_counter()
+        t_free = 0.0
+        for i in range(nreq):
+            wait = arrivals[i] - (time.perf_counter() - start)
+            if wait > 0:
+                time.sleep(wait)
+            plain_one(i)
+            lat.append(time.perf_counter() - start - arrivals[i])
+        wall = time.perf_counter() - start
+        lat = np.array(lat) * 1e3
+        sp = {"keys_per_s": total / wall, "p50_ms": float(np.percentile(lat, 50)),
+              "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "wall_s": wall}
+        out["loads"][str(load)] = {"arrival_rate_req_s": lam, "batched": sb, "plain": sp}
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -335,6 +468,14 @@ def run_gpu(args):
         ok_e2e = bool(np.all(hk_out.numpy()[1:] >= hk_out.numpy()[:-1]))
         line["e2e"]["sorted_check"] = ok_e2e
 
+    if rank == 0 and ws == 1 and not args.no_batched:
+        del copies
+        torch.cuda.empty_cache()
+        line["batched"] = measure_batched(ps, dev, args.batched_segments)
+        torch.cuda.empty_cache()
+    if rank == 0 and ws == 1 and not args.no_serving:
+        line["serving"] = measure_serving(ps, dev, args.serving_requests)
+        torch.cuda.empty_cache()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = _cpu_baseline(keys, vals, f"one full n={n} input of the same workload, "
                                                          "oracle powersort (Alg. 2), single thread")
@@ -354,6 +495,10 @@ def main():
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="array size (default 1e8)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 10,000-array batched measurement")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--batched-segments", type=int, default=10000)
+    ap.add_argument("--serving-requests", type=int, default=300)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.impl == "reference":

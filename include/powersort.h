@@ -16,9 +16,10 @@
  * Conventions for every entry point:
  *   - Pointers named d_* or documented as "device" are CUDA device pointers owned by the caller;
  *     the library never frees caller memory.  "host" pointers are ordinary host memory.
- *   - keys and vals must be 16-byte aligned (cudaMalloc / PyTorch allocations are).  Bulk copies
- *     may read, but never write, up to 15 bytes past the end of either array inside its last
- *     16-byte block.
+ *   - keys and vals need their natural alignment (key size, 4 bytes); sub-arrays at any element
+ *     offset are fine.  Bulk copies work on whole 16-byte blocks, so a kernel may read, but never
+ *     write, up to 15 bytes before the first or after the last element of an array, inside the
+ *     16-byte blocks that hold its first and last elements.
  *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).  Sorting calls
  *     are stream-ordered: they return once all work is enqueued; argument errors are returned
  *     synchronously.  Each sort synchronizes the stream once, after planning, to size its
@@ -73,7 +74,7 @@ size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented);
 /* Stable in-place sort of keys[0..n) (device, key_type elements) carrying vals[0..n) (device
  * uint32 payload, or NULL), powersort merge order (Alg. 2).  workspace: device memory of at least
  * ps_workspace_size(key_type, vals != NULL, n, 0) bytes, 256-byte aligned, caller-owned.
- * n = 0 or 1 is a no-op.  Errors: PS_ERR_INVALID_ARG (null/misaligned pointers, n < 0, unknown
+ * n = 0 or 1 is a no-op.  Errors: PS_ERR_INVALID_ARG (null or misaligned pointers, n < 0, unknown
  * key type), PS_ERR_OUT_OF_MEMORY (workspace too small), PS_ERR_UNSUPPORTED (n >= 2^31),
  * PS_ERR_CUDA, PS_ERR_TIMEOUT. */
 ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,

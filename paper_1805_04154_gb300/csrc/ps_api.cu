@@ -158,8 +158,6 @@ struct AnalyzeOut {
   ps_stats* stats;
 };
 
-bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
-
 // Level-pass ring depth: PS_PASS_STAGES (2, 3, 4 or 6) overrides the default for tuning runs.
 int pass_stages_setting() {
   static int v = -1;
@@ -187,8 +185,8 @@ ps_status check_args(int kt, const void* keys, const uint32_t* vals, int64_t n) 
   if (!launch_for(kt)) return PS_ERR_INVALID_ARG;
   if (n < 0) return PS_ERR_INVALID_ARG;
   if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
-  if (n > 0 && (!keys || !aligned16(keys))) return PS_ERR_INVALID_ARG;
-  if (vals && !aligned16(vals)) return PS_ERR_INVALID_ARG;
+  if (n > 0 && (!keys || ((uintptr_t)keys % (uintptr_t)key_bytes(kt)) != 0)) return PS_ERR_INVALID_ARG;
+  if (vals && ((uintptr_t)vals & 3u) != 0) return PS_ERR_INVALID_ARG;
   return PS_OK;
 }
 

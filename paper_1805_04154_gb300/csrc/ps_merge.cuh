@@ -357,6 +357,17 @@ __device__ __forceinline__ bool consumer_all(bool p) {
   return r != 0;
 }
 
+// Element range [e0, e1) of base widened to whole 16-byte blocks: [c0, c1) (element indices,
+// possibly c0 < 0 by a few elements when base itself is not 16-byte aligned).  Empty ranges give
+// an empty chunk.  Needs base aligned to sizeof(E).
+template <class E>
+__device__ __forceinline__ void chunk16(const E* base, int32_t e0, int32_t e1, int32_t& c0, int32_t& c1) {
+  constexpr int kPer = 16 / (int)sizeof(E);
+  const int32_t phase = (int32_t)(((uintptr_t)base & 15u) / sizeof(E));  // elements before base in its block
+  c0 = ((e0 + phase) & ~(kPer - 1)) - phase;
+  c1 = (e1 > e0) ? (((e1 + phase + kPer - 1) & ~(kPer - 1)) - phase) : c0;
+}
+
 __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
   uint32_t tries = 0;
   while (!mbar_try_wait(bar, parity))
@@ -509,10 +520,14 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             if (lane == 0) {
               const int32_t a0 = cnd.x + ti0, a1 = cnd.x + ti1;
               const int32_t b0 = cnd.y + (tg0 - cnd.x - ti0), b1 = cnd.y + (tg1 - cnd.x - ti1);
-              const int32_t ka0 = a0 & ~(KU - 1), ka1 = (a1 > a0) ? ((a1 + KU - 1) & ~(KU - 1)) : ka0;
-              const int32_t kb0 = b0 & ~(KU - 1), kb1 = (b1 > b0) ? ((b1 + KU - 1) & ~(KU - 1)) : kb0;
-              const int32_t va0 = a0 & ~3, va1 = (a1 > a0) ? ((a1 + 3) & ~3) : va0;
-              const int32_t vb0 = b0 & ~3, vb1 = (b1 > b0) ? ((b1 + 3) & ~3) : vb0;
+              // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only
+              // need natural alignment; a chunk may start up to 15 bytes before a range and end up
+              // to 15 bytes after it, always inside 16-byte blocks holding range elements)
+              int32_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
+              chunk16(srck, a0, a1, ka0, ka1);
+              chunk16(srck, b0, b1, kb0, kb1);
+              chunk16(srcv, a0, a1, va0, va1);
+              chunk16(srcv, b0, b1, vb0, vb1);
               StageDesc d;
               d.g0 = tg0;
               d.g1 = tg1;
@@ -639,7 +654,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           }
         }
         const int32_t g = d.g0 + diag;
-        if (cnt == kMergeItems && (g % KU) == 0) {
+        if (cnt == kMergeItems && ((uintptr_t)(dstk + g) & 15u) == 0) {
           uint4* o = (uint4*)(dstk + g);
 #pragma unroll
           for (int q = 0; q < kMergeItems / KU; ++q) {
@@ -655,7 +670,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             if (q < cnt) dstk[g + q] = key[q];
         }
         if (V) {
-          if (cnt == kMergeItems && (g % 4) == 0) {
+          if (cnt == kMergeItems && ((uintptr_t)(dstv + g) & 15u) == 0) {
             uint4* o = (uint4*)(dstv + g);
 #pragma unroll
             for (int q = 0; q < kMergeItems / 4; ++q)

@@ -55,8 +55,9 @@ def test_argument_errors_without_gpu(lib):
     # unknown key type, negative n, misaligned pointer, too large n: rejected before any CUDA call
     assert lib.ps_sort_ws(9, ctypes.c_void_p(4096), None, 10, ws, 1 << 20, None) == 1
     assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, -1, ws, 1 << 20, None) == 1
-    assert lib.ps_sort_ws(0, ctypes.c_void_p(4100), None, 10, ws, 1 << 20, None) == 1
-    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), ctypes.c_void_p(4104), 10, ws, 1 << 20, None) == 1
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4098), None, 10, ws, 1 << 20, None) == 1  # int32 needs 4 B
+    assert lib.ps_sort_ws(2, ctypes.c_void_p(4100), None, 10, ws, 1 << 20, None) == 1  # uint64 needs 8 B
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), ctypes.c_void_p(4106), 10, ws, 1 << 20, None) == 1
     assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1 << 31, ws, 1 << 20, None) == 2
     assert lib.ps_workspace_size(0, 1, 1000, 0) > 1000 * 8
     assert lib.ps_workspace_size(7, 1, 1000, 0) == 0

@@ -203,3 +203,29 @@ def test_pool_entry_point_and_stats(ps):
     assert ps.ps_stream_status() == 0
     np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
     np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+
+
+@pytest.mark.parametrize("kt,off", [("i32", 1), ("i32", 3), ("u64", 1), ("f32", 2)])
+def test_unaligned_subarray_views(ps, kt, off):
+    """Sub-arrays at element offsets that are not 16-byte aligned: sorted bit-exactly, and the
+    elements around the view are left untouched."""
+    n = 70001
+    if kt == "u64":
+        keys, vals = workloads.pareto_u64(n, seed=off, distinct=50)
+    elif kt == "f32":
+        keys, vals = workloads.pareto_f32(n, seed=off)
+    else:
+        keys, vals = workloads.runs_i32(n, seed=off, max_len=900)
+    ref = oracle.powersort(keys, vals, kt=kt)
+    pad = np.zeros(off, dtype=keys.dtype)
+    big_k = _to_dev(np.concatenate([pad, keys, pad]))
+    big_v = _to_dev(np.concatenate([np.full(off, 7, np.uint32), vals, np.full(off, 9, np.uint32)]))
+    dk, dv = big_k[off:off + n], big_v[off:off + n]
+    ps.ps_sort(dk, dv, key_type=KT_NAME[kt])
+    assert ps.ps_stream_status() == 0
+    hk = big_k.cpu().numpy().view(keys.dtype)
+    hv = big_v.cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(hk[off:off + n], ref.keys)
+    np.testing.assert_array_equal(hv[off:off + n], ref.vals)
+    assert (hk[:off] == 0).all() and (hk[off + n:] == 0).all()
+    assert (hv[:off] == 7).all() and (hv[off + n:] == 9).all()
