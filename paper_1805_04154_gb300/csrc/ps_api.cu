@@ -54,6 +54,10 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.ldepth = (uint8_t*)take(N);
   c.detect_tiles = (int32_t)((n + kDetectTile - 1) / kDetectTile);
   c.detect_state = (uint64_t*)take((size_t)std::max<int32_t>(c.detect_tiles, 1) * 16);  // functions + prefixes
+  const size_t dthreads = (size_t)std::max<int32_t>(c.detect_tiles, 1) * kDetectThreads;
+  c.thr_L = (uint64_t*)take(dthreads * 8);
+  c.thr_F = segmented ? (uint64_t*)take(dthreads * 8) : nullptr;
+  c.thr_fn = (uint32_t*)take(dthreads * 4);
   const size_t tree_tiles = (size_t)(n + 1) / kTreeTile + 1;
   c.tree_sum = (int32_t*)take(tree_tiles * 32 * 4);
   c.tree_pre = (int32_t*)take(tree_tiles * 32 * 4);
@@ -232,7 +236,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     StageTimer t(0, s);
     if (segmented) PS_TRY(launch_check_offsets(c));
     PS_TRY(kl->detect(c));
-    t.done(2 * (uint64_t)n * c.key_bytes, segmented ? 4 : 3);
+    t.done((uint64_t)n * c.key_bytes, segmented ? 4 : 3);
   }
   {
     StageTimer t(1, s);

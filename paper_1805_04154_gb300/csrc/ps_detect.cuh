@@ -63,6 +63,14 @@ __device__ __forceinline__ Fn unpack_agg(uint64_t w) {
             (uint32_t)((w >> 40) & 0xffffu)};
 }
 
+// Thread function word: map in [5:0], c0/c1/c2 in 6-bit fields at 6, 12, 18 (counts <= 32).
+__device__ __forceinline__ uint32_t pack_thread_fn(const Fn& f) {
+  return f.map | (f.c0 << 6) | (f.c1 << 12) | (f.c2 << 18);
+}
+__device__ __forceinline__ Fn unpack_thread_fn(uint32_t w) {
+  return Fn{w & 63u, (w >> 6) & 63u, (w >> 12) & 63u, (w >> 18) & 63u};
+}
+
 // Largest k with offsets[k] <= p (the segment containing p when segments are non-empty).
 __device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t count, int32_t p) {
   int32_t lo = 0, hi = count;  // offsets[0] = 0 <= p
@@ -132,6 +140,14 @@ struct ThreadRuns {
       }
     }
   }
+  // rebuild the view from the pair / forced-start masks the reduce pass saved
+  __device__ __forceinline__ void restore(int32_t n, int32_t tile, int tid, uint64_t l, uint64_t f) {
+    p0 = tile * kDetectTile + tid * kDetectItems;
+    nvalid = max(0, min(kDetectItems, n - p0));
+    valid = (nvalid >= 64) ? ~0ull : ((1ull << nvalid) - 1ull);
+    L = l;
+    F = f;
+  }
   // first run start at or after position 0 for a run entered with direction e (1 = ascending)
   __device__ __forceinline__ int first_start(uint32_t e) const {
     const uint64_t c = (((e ? ~L : L)) | F) & valid;
@@ -186,12 +202,18 @@ struct ThreadRuns {
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
 detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
-                     int32_t count, uint64_t* __restrict__ tile_agg) {
+                     int32_t count, uint64_t* __restrict__ tile_agg, uint64_t* __restrict__ thr_L,
+                     uint64_t* __restrict__ thr_F, uint32_t* __restrict__ thr_fn) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ThreadRuns<K> tr;
   tr.load(keys, n, offsets, count, blockIdx.x, tid);
   Fn incl = tr.aggregate();
+  // the emit pass replays the runs from these instead of reading the keys again
+  const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
+  thr_L[gt] = tr.L;
+  if (offsets != nullptr) thr_F[gt] = tr.F;
+  thr_fn[gt] = pack_thread_fn(incl);
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
     const Fn up = fn_shfl_up(incl, d);
@@ -248,14 +270,16 @@ detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int32_
 // S[k], directions run_desc[k] and segments run_seg[k] at their global ranks.
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
-detect_emit_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
-                   int32_t count, const uint64_t* __restrict__ tile_pre, int32_t* __restrict__ S,
-                   uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
+detect_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count,
+                   const uint64_t* __restrict__ tile_pre, const uint64_t* __restrict__ thr_L,
+                   const uint64_t* __restrict__ thr_F, const uint32_t* __restrict__ thr_fn,
+                   int32_t* __restrict__ S, uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
   ThreadRuns<K> tr;
-  tr.load(keys, n, offsets, count, blockIdx.x, tid);
-  const Fn agg = tr.aggregate();
+  tr.restore(n, blockIdx.x, tid, thr_L[gt], offsets != nullptr ? thr_F[gt] : (blockIdx.x == 0 && tid == 0 ? 1ull : 0ull));
+  const Fn agg = unpack_thread_fn(thr_fn[gt]);
   Fn incl = agg;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {

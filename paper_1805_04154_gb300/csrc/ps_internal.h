@@ -34,6 +34,9 @@ struct Ctx {
 
   uint64_t* detect_state = nullptr;
   int32_t detect_tiles = 0;
+  uint64_t* thr_L = nullptr;    // per detection thread: pair bits of its 32 positions
+  uint64_t* thr_F = nullptr;    // forced-start bits (segmented calls only)
+  uint32_t* thr_fn = nullptr;   // its transition function with run counts
   int32_t* tree_sum = nullptr;  // [tree tiles][32]
   int32_t* tree_pre = nullptr;
 

@@ -15,12 +15,13 @@ struct Launch {
   typedef typename K::T T;
 
   static cudaError_t detect(const Ctx& c) {
-    detect_reduce_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>((const T*)c.k[0], c.n, c.offsets,
-                                                                              c.count, c.detect_state);
+    detect_reduce_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
+        (const T*)c.k[0], c.n, c.offsets, c.count, c.detect_state, c.thr_L, c.thr_F, c.thr_fn);
     detect_scan_kernel<<<1, 1024, 0, c.stream>>>(c.detect_state, c.detect_tiles, c.n, c.detect_state + c.detect_tiles,
                                                  c.S, c.hdr);
     detect_emit_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
-        (const T*)c.k[0], c.n, c.offsets, c.count, c.detect_state + c.detect_tiles, c.S, c.run_desc, c.run_seg);
+        c.n, c.offsets, c.count, c.detect_state + c.detect_tiles, c.thr_L, c.thr_F, c.thr_fn, c.S, c.run_desc,
+        c.run_seg);
     return cudaGetLastError();
   }
 

@@ -246,6 +246,7 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
                   const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                   const uint32_t* __restrict__ tile_off, uint32_t nitems) {
   typedef typename K::T T;
+  constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
   __shared__ int32_t s_slot;
   if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, blockIdx.x);
   __syncthreads();
@@ -254,27 +255,61 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
   const int32_t k = (int32_t)(blockIdx.x - tile_off[slot]);
   const int32_t s = S[i], e = S[i + 1];
   const bool desc = run_desc[i] != 0;
-  T* k0 = (T*)buf.k[0];
-  T* k1 = (T*)buf.k[1];
+  const T* __restrict__ k0 = (const T*)buf.k[0];
+  const uint32_t* __restrict__ v0 = buf.v[0];
+  // all loads of the thread first (independent, coalesced even when reversed), then the stores
+  T kx[kPer], ky[kPer];
+  uint32_t vx[kPer], vy[kPer];
   if (ldepth[i] & 1) {
-    const int32_t q1 = min(e, s + (k + 1) * kMergeTile);
-    for (int32_t q = s + k * kMergeTile + threadIdx.x; q < q1; q += blockDim.x) {
-      const int32_t src = desc ? s + e - 1 - q : q;
-      k1[q] = k0[src];
-      if (V) buf.v[1][q] = buf.v[0][src];
+    T* __restrict__ k1 = (T*)buf.k[1];
+    uint32_t* __restrict__ v1 = buf.v[1];
+    const int32_t q0 = s + k * kMergeTile + threadIdx.x, q1 = min(e, s + (k + 1) * kMergeTile);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int32_t q = q0 + u * 256;
+      if (q < q1) {
+        const int32_t src = desc ? s + e - 1 - q : q;
+        kx[u] = k0[src];
+        if (V) vx[u] = v0[src];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int32_t q = q0 + u * 256;
+      if (q < q1) {
+        k1[q] = kx[u];
+        if (V) v1[q] = vx[u];
+      }
     }
   } else {
+    T* kk = (T*)buf.k[0];
+    uint32_t* vv = buf.v[0];
     const int32_t half = (e - s) / 2;
-    const int32_t p1 = min(s + half, s + (k + 1) * kMergeTile);
-    for (int32_t p = s + k * kMergeTile + threadIdx.x; p < p1; p += blockDim.x) {
-      const int32_t q = s + e - 1 - p;
-      const T a = k0[p], b = k0[q];
-      k0[p] = b;
-      k0[q] = a;
-      if (V) {
-        const uint32_t va = buf.v[0][p], vb = buf.v[0][q];
-        buf.v[0][p] = vb;
-        buf.v[0][q] = va;
+    const int32_t p0 = s + k * kMergeTile + threadIdx.x, p1 = min(s + half, s + (k + 1) * kMergeTile);
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int32_t p = p0 + u * 256;
+      if (p < p1) {
+        const int32_t q = s + e - 1 - p;
+        kx[u] = kk[p];
+        ky[u] = kk[q];
+        if (V) {
+          vx[u] = vv[p];
+          vy[u] = vv[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int32_t p = p0 + u * 256;
+      if (p < p1) {
+        const int32_t q = s + e - 1 - p;
+        kk[p] = ky[u];
+        kk[q] = kx[u];
+        if (V) {
+          vv[p] = vy[u];
+          vv[q] = vx[u];
+        }
       }
     }
   }
