@@ -401,7 +401,7 @@ def run_gpu(args):
     mt = prof["level_pass"]
     achieved = (mt["bytes"] / (mt["ms"] / 1000.0) / 1e9) if mt["ms"] > 0 else None
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "merge_tile_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", "level_pass_traffic.json")
     if os.path.exists(tpath):
         try:
             import hashlib
