@@ -125,6 +125,35 @@ def _cpu_baseline(keys, vals, sample_desc: str):
             "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
 
 
+def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5):
+    """Sort throughput of one more workload (resident inputs, fresh copy per step)."""
+    import numpy as np
+    import torch
+    eb = keys.dtype.itemsize + 4
+    k0 = torch.from_numpy(keys.view({4: np.int32, 8: np.int64}[keys.dtype.itemsize])).to(dev)
+    v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
+    an = ps.ps_analyze(k0, key_type=kt)
+    n = keys.size
+    ws = torch.empty(ps.ps_workspace_size(kt, True, n), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    copies = [(k0.clone(), v0.clone()) for _ in range(steps + 2)]
+    for i in range(2):
+        ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(2, steps + 2):
+        ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / steps
+    peak, _ = _peaks()
+    ideal = an["cost"] * eb * 2 / (peak * 1e9) * 1e3
+    del copies, ws, k0, v0
+    return {"workload": name, "n": int(n), "runs": int(an["runs"]), "merge_cost": int(an["cost"]),
+            "ms_per_sort": ms, "gkeys_s": n / (ms / 1e3) / 1e9, "merge_cost_roofline_frac": ideal / ms}
+
+
 def measure_batched(ps, dev, count: int, reps: int = 3):
     """10,000 uneven int32 arrays (sizes floor(2^U(8,20)), runs uniform in [1, 2 sqrt(size)])
     sorted in one segmented call vs one plain call per array, same device-resident inputs."""
@@ -468,8 +497,24 @@ def run_gpu(args):
         ok_e2e = bool(np.all(hk_out.numpy()[1:] >= hk_out.numpy()[:-1]))
         line["e2e"]["sorted_check"] = ok_e2e
 
-    if rank == 0 and ws == 1 and not args.no_batched:
+    if rank == 0 and ws == 1 and not args.no_variants:
+        import workloads
         del copies
+        torch.cuda.empty_cache()
+        var = []
+        pk, pv = workloads.perm_i32(n, seed=SEED)
+        var.append(measure_variant(ps, dev, f"random permutation, n={n} int32 + uint32 (runs ~2.4)", pk, pv, 0))
+        del pk, pv
+        rk, rv = workloads.random_runs_i32(10 ** 7, seed=SEED, mean_len=3000)
+        var.append(measure_variant(ps, dev, "paper random-runs: n=1e7, geometric run lengths, mean 3000", rk, rv, 0))
+        uk, uv = workloads.pareto_u64(n, seed=SEED, alpha=1.2, distinct=1000, max_len=n // 10)
+        var.append(measure_variant(ps, dev, f"uint64 keys from 1000 values, Pareto(1.2) runs, n={n} + uint32", uk, uv, 2))
+        del uk, uv
+        line["variants"] = var
+        torch.cuda.empty_cache()
+        copies = None
+    if rank == 0 and ws == 1 and not args.no_batched:
+        copies = None
         torch.cuda.empty_cache()
         line["batched"] = measure_batched(ps, dev, args.batched_segments)
         torch.cuda.empty_cache()
@@ -496,6 +541,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 10,000-array batched measurement")
+    ap.add_argument("--no-variants", action="store_true", help="skip the other single-array workloads")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--batched-segments", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=300)
