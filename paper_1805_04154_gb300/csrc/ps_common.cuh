@@ -44,12 +44,14 @@ struct KeyI32 {
   typedef uint32_t T;
   static constexpr int kType = 0;
   __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x ^ 0x80000000u; }
+  __device__ __forceinline__ static uint32_t unord(uint32_t u) { return u ^ 0x80000000u; }
   __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return (int32_t)a <= (int32_t)b; }
 };
 struct KeyU32 {
   typedef uint32_t T;
   static constexpr int kType = 1;
   __device__ __forceinline__ static uint32_t ord(uint32_t x) { return x; }
+  __device__ __forceinline__ static uint32_t unord(uint32_t u) { return u; }
   __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return a <= b; }
 };
 struct KeyU64 {
@@ -63,6 +65,10 @@ struct KeyF32 {
   static constexpr int kType = 3;
   __device__ __forceinline__ static uint32_t ord(uint32_t x) {
     return x ^ ((uint32_t)((int32_t)x >> 31) | 0x80000000u);
+  }
+  // inverse of ord: a set top bit marks a non-negative pattern
+  __device__ __forceinline__ static uint32_t unord(uint32_t u) {
+    return u ^ ((uint32_t)((int32_t)~u >> 31) | 0x80000000u);
   }
   __device__ __forceinline__ static bool le(uint32_t a, uint32_t b) { return ord(a) <= ord(b); }
 };

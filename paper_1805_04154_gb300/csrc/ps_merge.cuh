@@ -46,119 +46,231 @@ __device__ __forceinline__ int32_t corank_serial(TA A, TB B, int32_t la, int32_t
 
 // ---------------------------------------------------------------------------------------
 // Whole subtree in shared memory.
+//
+// The task's elements stay in one shared-memory array from the leaves to the subtree root.
+// Each level's merges are computed into registers (thread t produces the outputs at positions
+// [t*IPT, t*IPT + IPT)), the block synchronises, and the outputs overwrite their positions, so
+// one array suffices and buffer parity plays no role inside the task.  Every element carries
+// its position inside the task; as all elements of a left child sit before all elements of the
+// right child, "the left element goes first on equal keys" is the order of (key, position):
+//  * 4-byte keys: one 64-bit word (order-mapped key << 32 | position) compared as an integer;
+//  * 8-byte keys: the key and a 32-bit position side by side, keys compared with the tie rule.
+// The payload does not move during the merges: it is staged once at the end and gathered
+// through the positions.  The array has one padding slot per IPT elements, so the IPT-strided
+// accesses of a warp fall into distinct banks.
 // ---------------------------------------------------------------------------------------
-template <class K, bool V>
-struct SubLayout {
-  typedef typename K::T T;
-  static constexpr int TS = sub_tile((int)sizeof(T));
-  static constexpr int RC = TS / 2 + 2;  // runs in a task: all but a segment's last have length >= 2
+template <class K, int KB = (int)sizeof(typename K::T)>
+struct SubElem;
+
+template <class K>
+struct SubElem<K, 4> {
+  typedef uint64_t R;
+  static constexpr int TS = sub_tile(4);
   static constexpr int IPT = TS / kSubThreads;
-  static constexpr size_t kKeys = 2 * (size_t)TS * sizeof(T);
-  static constexpr size_t kVals = V ? 2 * (size_t)TS * 4 : 0;
-  static constexpr size_t kMeta = (size_t)RC * (2 + 2 + 2 + 2 + 1 + 1);
-  static constexpr size_t kBytes = kKeys + kVals + kMeta;
+  static constexpr int kPadded = TS + TS / IPT;
+  static constexpr size_t kDataBytes = (size_t)kPadded * 8;
+  struct Arr {
+    uint64_t* w;
+  };
+  __device__ __forceinline__ static Arr arr(uint8_t* base) { return Arr{(uint64_t*)base}; }
+  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) { return a.w[i]; }
+  __device__ __forceinline__ static void st(const Arr& a, int32_t i, R x) { a.w[i] = x; }
+  __device__ __forceinline__ static R make(uint32_t key, int32_t pos) {
+    return ((uint64_t)K::ord(key) << 32) | (uint32_t)pos;
+  }
+  // positions differ, so two elements never compare equal
+  __device__ __forceinline__ static bool before(R a, R b) { return a < b; }
+  __device__ __forceinline__ static uint32_t key(R x) { return K::unord((uint32_t)(x >> 32)); }
+  __device__ __forceinline__ static int32_t pos(R x) { return (int32_t)(uint32_t)x; }
 };
 
+template <class K>
+struct SubElem<K, 8> {
+  struct R {
+    uint64_t k;
+    uint32_t p;
+  };
+  static constexpr int TS = sub_tile(8);
+  static constexpr int IPT = TS / kSubThreads;
+  static constexpr int kPadded = TS + TS / IPT;
+  static constexpr size_t kDataBytes = (size_t)kPadded * 12;
+  struct Arr {
+    uint64_t* k;
+    uint32_t* p;
+  };
+  __device__ __forceinline__ static Arr arr(uint8_t* base) {
+    return Arr{(uint64_t*)base, (uint32_t*)(base + (size_t)kPadded * 8)};
+  }
+  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) { return R{a.k[i], a.p[i]}; }
+  __device__ __forceinline__ static void st(const Arr& a, int32_t i, R x) {
+    a.k[i] = x.k;
+    a.p[i] = x.p;
+  }
+  __device__ __forceinline__ static R make(uint64_t key, int32_t pos) { return R{key, (uint32_t)pos}; }
+  // a comes from the left child: it goes first unless its key is greater
+  __device__ __forceinline__ static bool before(const R& a, const R& b) { return K::le(a.k, b.k); }
+  __device__ __forceinline__ static uint64_t key(const R& x) { return x.k; }
+  __device__ __forceinline__ static int32_t pos(const R& x) { return (int32_t)x.p; }
+};
+
+// padded slot of position p
+template <class E>
+__device__ __forceinline__ int32_t sub_slot(int32_t p) {
+  return p + p / E::IPT;
+}
+
 template <class K, bool V>
-__global__ void __launch_bounds__(kSubThreads)
+struct SubLayout {
+  typedef SubElem<K> E;
+  static constexpr int TS = E::TS;
+  static constexpr int RC = TS / 2 + 2;  // runs in a task: all but a segment's last have length >= 2
+  // The region after the element array holds in turn: run starts and directions (leaf
+  // placement), the level-sorted node list (merges), the staged payload (write-out).
+  static constexpr size_t kRuns = (size_t)RC * 3;
+  static constexpr size_t kNodes = (size_t)RC * 8;
+  static constexpr size_t kPay = V ? (size_t)TS * 4 : 0;
+  static constexpr size_t kMeta = kNodes > kPay ? kNodes : kPay;
+  static_assert(kRuns <= kMeta, "run metadata fits the shared region");
+  static constexpr size_t kBytes = E::kDataBytes + kMeta;
+};
+
+// co-rank of output diag in the merge of positions [l, mm) and [mm, h) of the task array
+template <class E>
+__device__ __forceinline__ int32_t sub_corank(const typename E::Arr& X, int32_t l, int32_t mm, int32_t h,
+                                              int32_t diag) {
+  int32_t lo = max(0, diag - (h - mm)), hi = min(diag, mm - l);
+  while (lo < hi) {
+    const int32_t mid = (lo + hi) >> 1;
+    if (E::before(E::ld(X, sub_slot<E>(l + mid)), E::ld(X, sub_slot<E>(mm + diag - 1 - mid)))) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+template <class K, bool V>
+__global__ void __launch_bounds__(kSubThreads, 4)
 subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
                const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
   typedef typename K::T T;
+  typedef SubElem<K> E;
+  typedef typename E::R R;
   typedef SubLayout<K, V> Lay;
-  constexpr int TS = Lay::TS, RC = Lay::RC, IPT = Lay::IPT;
+  constexpr int TS = E::TS, IPT = E::IPT, RC = Lay::RC, NW = kSubThreads / 32;
+  static_assert(kMaxLevels * NW == kSubThreads, "one thread per (depth, warp) pair");
+  static_assert(IPT <= 32, "valid-output mask is 32 bits");
   extern __shared__ __align__(128) uint8_t smem[];
-  T* sk[2] = {(T*)smem, (T*)smem + TS};
-  uint32_t* sv[2] = {nullptr, nullptr};
-  uint8_t* meta = smem + Lay::kKeys;
-  if (V) {
-    sv[0] = (uint32_t*)(smem + Lay::kKeys);
-    sv[1] = sv[0] + TS;
-    meta += Lay::kVals;
-  }
-  int16_t* rs = (int16_t*)meta;   // local run starts, rs[nr] = m
-  int16_t* nlo = rs + RC;         // node b: local [nlo, rs[b], nhi)
-  int16_t* nhi = nlo + RC;
-  int16_t* lvl = nhi + RC;        // boundaries of the current level, by position
-  uint8_t* rinfo = (uint8_t*)(lvl + RC);  // leaf: (relative depth << 1) | descending
-  uint8_t* nrd = rinfo + RC;              // node relative depth
-  __shared__ int32_t s_wsum[kSubThreads / 32];
+  const typename E::Arr X = E::arr(smem);
+  uint8_t* meta = smem + E::kDataBytes;
+  __shared__ int32_t s_cnt[NW][kMaxLevels];  // boundaries per (warp, relative depth), then offsets
+  __shared__ int32_t s_lvl[kMaxLevels + 1];  // nodes of relative depth d: entries [s_lvl[d], s_lvl[d+1])
+  __shared__ int32_t s_wsum[NW];
   __shared__ int32_t s_maxrd;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t task = tasks[blockIdx.x];
-  int32_t L, R, droot;
+  int32_t L, R_, droot;
   if (task >= 0) {
     L = nodeL[task];
-    R = nodeR[task];
+    R_ = nodeR[task];
     droot = ndepth[task];
   } else {
     L = ~task;
-    R = L + 1;
+    R_ = L + 1;
     droot = ldepth[L];
   }
-  const int32_t lo = S[L], m = S[R] - lo, nr = R - L;
+  const int32_t lo = S[L], m = S[R_] - lo, nr = R_ - L;
   if (m > TS || nr + 1 > RC) {  // cannot happen for a greedy run partition; never overrun SMEM
     if (tid == 0) post_status(&hdr->status, lib_status, kDevInternal);
     return;
   }
-  if (tid == 0) s_maxrd = 0;
-  __syncthreads();
-  int my_max = 0;
+
+  // 1. run starts and directions; the keys, tagged with their positions
+  int16_t* rs = (int16_t*)meta;
+  uint8_t* rdsc = (uint8_t*)(rs + RC);
+  bool any_desc = false;
   for (int32_t k = tid; k <= nr; k += kSubThreads) {
     rs[k] = (int16_t)(S[L + k] - lo);
     if (k < nr) {
-      const int rd = (int)ldepth[L + k] - droot;
-      rinfo[k] = (uint8_t)((rd << 1) | (run_desc[L + k] ? 1 : 0));
-      my_max = max(my_max, rd);
-    }
-    if (k >= 1 && k < nr) {
-      const int32_t j = L + k;
-      nlo[k] = (int16_t)(S[nodeL[j]] - lo);
-      nhi[k] = (int16_t)(S[nodeR[j]] - lo);
-      nrd[k] = (uint8_t)((int)ndepth[j] - droot);
+      rdsc[k] = run_desc[L + k];
+      any_desc |= rdsc[k] != 0;
     }
   }
-  my_max = __reduce_max_sync(0xffffffffu, my_max);
-  if (lane == 0) atomicMax(&s_maxrd, my_max);
-  __syncthreads();
+  const T* __restrict__ gk = (const T*)buf.k[0];
+#pragma unroll
+  for (int u = 0; u < IPT; ++u) {
+    const int32_t p = tid + u * kSubThreads;
+    if (p < m) E::st(X, sub_slot<E>(p), E::make(gk[lo + p], p));
+  }
+  for (int t = tid; t < NW * kMaxLevels; t += kSubThreads) (&s_cnt[0][0])[t] = 0;
+  if (tid == 0) s_maxrd = -1;
+  const int anyd = __syncthreads_or(any_desc);
 
-  // place the leaves: leaf at relative depth d goes to buffer d mod 2, reversed if descending
-  const T* gk = (const T*)buf.k[0];
-  const uint32_t* gv = buf.v[0];
-  {
-    const int32_t p0 = tid * IPT;
-    if (p0 < m) {
-      int32_t a = 0, b = nr;  // run containing p0: largest k with rs[k] <= p0
+  // 2. descending runs reversed in place, through registers
+  const int32_t cs = tid * IPT;
+  if (anyd) {
+    R v[IPT];
+    uint32_t mv = 0;
+    if (cs < m) {
+      int32_t a = 0, b = nr;  // run containing cs: largest k with rs[k] <= cs
       while (b - a > 1) {
         const int32_t mid = (a + b) >> 1;
-        if (rs[mid] <= p0) a = mid; else b = mid;
+        if (rs[mid] <= cs) a = mid;
+        else b = mid;
       }
       int32_t k = a;
 #pragma unroll
       for (int q = 0; q < IPT; ++q) {
-        const int32_t p = p0 + q;
+        const int32_t p = cs + q;
         if (p < m) {
           while (p >= rs[k + 1]) ++k;
-          const uint8_t info = rinfo[k];
-          const int32_t tgt = (info & 1) ? (int32_t)rs[k] + rs[k + 1] - 1 - p : p;
-          const int bsel = (info >> 1) & 1;
-          sk[bsel][tgt] = gk[lo + p];
-          if (V) sv[bsel][tgt] = gv[lo + p];
+          if (rdsc[k]) {
+            const int32_t src = (int32_t)rs[k] + rs[k + 1] - 1 - p;
+            if (src != p) {
+              v[q] = E::ld(X, sub_slot<E>(src));
+              mv |= 1u << q;
+            }
+          }
         }
       }
     }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+      if ((mv >> q) & 1u) E::st(X, sub_slot<E>(cs + q), v[q]);
   }
-  __syncthreads();
 
-  const int32_t nb = nr - 1;                              // boundaries 1..nr-1
-  const int32_t bpt = (nb + kSubThreads - 1) / kSubThreads;  // boundaries per thread
-  for (int rd = s_maxrd - 1; rd >= 0; --rd) {
-    // compact the boundaries of this level (in position order)
-    const int32_t b0 = 1 + tid * bpt, b1 = min(1 + (tid + 1) * bpt, nr);
-    int32_t c = 0;
-    for (int32_t bb = b0; bb < b1; ++bb) c += (nrd[bb] == rd);
+  // 3. the nodes (boundaries 1..nr-1), sorted by relative depth and by position inside a depth:
+  //    a counting sort over warp chunks (match_any groups a warp's equal depths)
+  const int32_t chunk = (nr - 1 + NW - 1) / NW;
+  const int32_t w0 = 1 + warp * chunk, w1 = min(1 + (warp + 1) * chunk, nr);
+  bool bad = false;
+  int my_max = -1;
+  for (int32_t k0 = w0; k0 < w1; k0 += 32) {
+    const int32_t k = k0 + lane;
+    int rd = kMaxLevels;  // lanes past the chunk form their own group
+    if (k < w1) {
+      rd = (int)ndepth[L + k] - droot;
+      if (rd < 0 || rd >= kMaxLevels) {
+        bad = true;
+        rd = 0;
+      }
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, rd);
+    if (k < w1) {
+      my_max = max(my_max, rd);
+      if (lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
+    }
+  }
+  if (bad) post_status(&hdr->status, lib_status, kDevInternal);
+  my_max = __reduce_max_sync(0xffffffffu, my_max);
+  if (lane == 0) atomicMax(&s_maxrd, my_max);
+  __syncthreads();
+  {
+    // exclusive scan in (depth, warp) order: thread t holds depth t / NW, warp t % NW
+    const int rd = tid / NW, w = tid % NW;
+    const int32_t c = s_cnt[w][rd];
     int32_t inc = c;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -167,62 +279,130 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
     }
     if (lane == 31) s_wsum[warp] = inc;
     __syncthreads();
-    int32_t off = inc - c, total = 0;
-    for (int w = 0; w < kSubThreads / 32; ++w) {
-      if (w < warp) off += s_wsum[w];
-      total += s_wsum[w];
+    int32_t off = inc - c;
+    for (int x = 0; x < warp; ++x) off += s_wsum[x];
+    s_cnt[w][rd] = off;
+    if (w == 0) s_lvl[rd] = off;
+    if (tid == kSubThreads - 1) s_lvl[kMaxLevels] = off + c;
+  }
+  __syncthreads();
+  uint64_t* ent = (uint64_t*)meta;  // node: lo | mid << 16 | hi << 32 (task-relative)
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int32_t k0 = w0; k0 < w1; k0 += 32) {
+    const int32_t k = k0 + lane;
+    int rd = kMaxLevels;
+    if (k < w1) rd = min(max((int)ndepth[L + k] - droot, 0), kMaxLevels - 1);
+    const uint32_t peers = __match_any_sync(0xffffffffu, rd);
+    if (k < w1) {
+      const int32_t j = L + k;
+      const int32_t at = s_cnt[warp][rd] + __popc(peers & lt_mask);
+      const uint32_t nlo = (uint32_t)(S[nodeL[j]] - lo), nmid = (uint32_t)(S[j] - lo);
+      const uint32_t nhi = (uint32_t)(S[nodeR[j]] - lo);
+      ent[at] = (uint64_t)(nlo | (nmid << 16)) | ((uint64_t)nhi << 32);
     }
-    for (int32_t bb = b0; bb < b1; ++bb)
-      if (nrd[bb] == rd) lvl[off++] = (int16_t)bb;
-    __syncthreads();
-    if (total == 0) continue;
+    __syncwarp();
+    if (k < w1 && lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
 
-    const T* srck = sk[(rd + 1) & 1];
-    T* dstk = sk[rd & 1];
-    const uint32_t* srcv = sv[(rd + 1) & 1];
-    uint32_t* dstv = sv[rd & 1];
-    const int32_t cs = tid * IPT, ce = min(m, cs + IPT);
-    if (cs < ce) {
-      int32_t a = 0, b = total;  // first node of the level with nhi > cs
+  // 4. the levels, deepest first
+  for (int rd = s_maxrd; rd >= 0; --rd) {
+    const int32_t e0 = s_lvl[rd], e1 = s_lvl[rd + 1];
+    if (e0 == e1) continue;  // uniform over the block
+    R out[IPT];
+    uint32_t valid = 0;
+    if (cs < m) {
+      int32_t a = e0, b = e1;  // first node of the level with hi > cs
       while (a < b) {
         const int32_t mid = (a + b) >> 1;
-        if (nhi[lvl[mid]] <= cs) a = mid + 1; else b = mid;
+        if ((int32_t)(ent[mid] >> 32) <= cs) a = mid + 1;
+        else b = mid;
       }
-      for (int32_t idx = a; idx < total; ++idx) {
-        const int32_t bnd = lvl[idx];
-        const int32_t l = nlo[bnd];
-        if (l >= ce) break;
-        const int32_t mm = rs[bnd], h = nhi[bnd];
-        const int32_t ps = max(cs, l), pe = min(ce, h);
-        if (ps >= pe) continue;
-        const T* A = srck + l;
-        const T* B = srck + mm;
-        const int32_t la = mm - l, lb = h - mm;
-        int32_t i = corank_serial<K>(A, B, la, lb, ps - l);
-        int32_t j = (ps - l) - i;
-        for (int32_t p = ps; p < pe; ++p) {
-          const bool takeA = (j >= lb) || (i < la && key_le<K>(A[i], B[j]));
-          if (takeA) {
-            dstk[p] = A[i];
-            if (V) dstv[p] = srcv[l + i];
-            ++i;
+      constexpr int32_t kNone = 1 << 30;
+      int32_t l = kNone, mm = kNone, h = kNone, ia = kNone, ib = kNone;
+      R va, vb;
+      if (a < e1) {
+        const uint64_t e = ent[a];
+        l = (int32_t)(e & 0xFFFFu);
+        mm = (int32_t)((e >> 16) & 0xFFFFu);
+        h = (int32_t)(e >> 32);
+        ia = l;
+        ib = mm;
+        if (l < cs) {
+          const int32_t diag = cs - l;
+          const int32_t i = sub_corank<E>(X, l, mm, h, diag);
+          ia = l + i;
+          ib = mm + diag - i;
+        }
+        if (ia < mm) va = E::ld(X, sub_slot<E>(ia));
+        if (ib < h) vb = E::ld(X, sub_slot<E>(ib));
+      }
+#pragma unroll
+      for (int q = 0; q < IPT; ++q) {
+        const int32_t p = cs + q;
+        if (p >= h) {  // this node is done; the level's next node starts at or after p
+          ++a;
+          if (a < e1) {
+            const uint64_t e = ent[a];
+            l = (int32_t)(e & 0xFFFFu);
+            mm = (int32_t)((e >> 16) & 0xFFFFu);
+            h = (int32_t)(e >> 32);
+            ia = l;
+            ib = mm;
+            va = E::ld(X, sub_slot<E>(l));
+            vb = E::ld(X, sub_slot<E>(mm));
           } else {
-            dstk[p] = B[j];
-            if (V) dstv[p] = srcv[mm + j];
-            ++j;
+            l = mm = h = kNone;
+          }
+        }
+        if (p >= l) {
+          const bool take = ia < mm && (ib >= h || E::before(va, vb));
+          out[q] = take ? va : vb;
+          valid |= 1u << q;
+          if (take) {
+            if (++ia < mm) va = E::ld(X, sub_slot<E>(ia));
+          } else {
+            if (++ib < h) vb = E::ld(X, sub_slot<E>(ib));
           }
         }
       }
     }
     __syncthreads();
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+      if ((valid >> q) & 1u) E::st(X, sub_slot<E>(cs + q), out[q]);
+    __syncthreads();
   }
 
-  // the subtree root (relative depth 0) sits in buffer 0; it belongs in global buffer droot mod 2
-  T* ok = (T*)buf.k[droot & 1];
-  uint32_t* ov = buf.v[droot & 1];
-  for (int32_t p = tid; p < m; p += kSubThreads) {
-    ok[lo + p] = sk[0][p];
-    if (V) ov[lo + p] = sv[0][p];
+  // 5. write-out: the subtree root belongs in global buffer droot mod 2
+  const bool odd = (droot & 1) != 0;  // (selects, not an indexed parameter array: no local copy)
+  T* __restrict__ ok = (T*)(odd ? buf.k[1] : buf.k[0]);
+  if (V) {
+    uint32_t* pay = (uint32_t*)meta;  // the node list is no longer needed
+    const uint32_t* __restrict__ gv = buf.v[0];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int32_t p = tid + u * kSubThreads;
+      if (p < m) pay[p] = gv[lo + p];
+    }
+    __syncthreads();
+    uint32_t* __restrict__ ov = odd ? buf.v[1] : buf.v[0];
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int32_t p = tid + u * kSubThreads;
+      if (p < m) {
+        const R x = E::ld(X, sub_slot<E>(p));
+        ok[lo + p] = E::key(x);
+        ov[lo + p] = pay[E::pos(x)];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < IPT; ++u) {
+      const int32_t p = tid + u * kSubThreads;
+      if (p < m) ok[lo + p] = E::key(E::ld(X, sub_slot<E>(p)));
+    }
   }
 }
 
