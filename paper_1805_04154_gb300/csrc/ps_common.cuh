@@ -19,10 +19,10 @@ constexpr int kDetectThreads = 256;
 constexpr int kDetectItems = 32;
 constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 8192
 
-// Stage 3 (nearest-smaller-value tree): 8 warps x 32 rounds x 32 boundaries per tile.
-constexpr int kTreeWarps = 8;
-constexpr int kTreeRounds = 32;
-constexpr int kTreeTile = kTreeWarps * kTreeRounds * 32;  // 8192
+// Stage 3 (nearest-smaller-value tree): 256 threads x 32 consecutive boundaries per tile.
+constexpr int kTreeThreads = 256;
+constexpr int kTreeChunk = 32;
+constexpr int kTreeTile = kTreeThreads * kTreeChunk;  // 8192
 
 // Stage 4 (merge passes over HBM): one CTA produces kMergeTile outputs of one merge.
 constexpr int kMergeThreads = 256;

@@ -47,83 +47,104 @@ __global__ void node_power_kernel(const int32_t* __restrict__ S, const int32_t* 
 // Stage 3: the merge tree (Corollary "Cartesian tree": the min-Cartesian tree of the powers).
 // For node j: Lj = nearest i < j with P_i < P_j, Rj = nearest k > j with P_k < P_j (the
 // power-0 sentinels and segment boundaries always qualify); node j merges [S[Lj], S[j]) with
-// [S[j], S[Rj]).  Its ancestors are exactly the "records" on either side: a boundary i < j is
-// an ancestor iff P_i is smaller than every power strictly between i and j and than P_j.  Among
-// positions of one power value only the last one before j can be a record, so with last[v] =
-// last index before j holding power v, the left ancestors are the v in [1, P_j) with
-// last[v] > max(last[0..v-1]), and Lj = max(last[0..P_j-1]).  The right side is the same on
-// reversed indices.  depth(j) = left records + right records (powers are < 32, so the 32
-// last[] entries live one per lane of a warp).
+// [S[j], S[Rj]).  Its ancestors are exactly the entries of the nearest-smaller-value stacks on
+// either side, so depth(j) = (left stack entries of power >= 1) + (right ones).
 //
-// The scan over last[] vectors runs in three kernels per direction: per-tile summaries, an
-// exclusive max-scan over tiles, and the apply pass.  Virtual index u maps to boundary
-// j = u (forward) or j = r - u (backward).
+// Left to right, the stack of nearest smaller values holds at most one entry per power value
+// (powers increase from its bottom), and an entry of power v is always the last boundary of
+// power v seen so far.  So a stack is a 32-bit occupancy mask plus the table last[v] = last
+// index of power v, and from last[] alone the stack is recovered: v is on it iff last[v] is
+// larger than last[w] for every w < v.  Thread-chunk and tile summaries are therefore last[]
+// vectors, combined by element-wise max.
+//
+// Per direction three kernels: per-tile last[] summaries, an exclusive max-scan over tiles,
+// and the apply pass in which each of kTreeThreads threads rebuilds the stack in front of its
+// kTreeChunk consecutive indices and walks them.  Virtual index u maps to boundary j = u
+// (forward) or j = r - u (backward).
 // ---------------------------------------------------------------------------------------
 template <bool kBackward>
 __device__ __forceinline__ int32_t virt_to_j(int32_t u, int32_t r) {
   return kBackward ? r - u : u;
 }
 
-// Per-warp pass over kTreeRounds rounds of 32 virtual indices starting at u0.  Updates carry
-// (lane v = last virtual index < current with power v, or -1).  If kApply, also emits L/R and
-// record counts for every node.
-template <bool kBackward, bool kApply>
-__device__ __forceinline__ void tree_warp_rounds(const uint8_t* __restrict__ P, int32_t r, int32_t u0,
-                                                 int32_t& carry, int32_t* __restrict__ near_out,
-                                                 uint8_t* __restrict__ depth_acc) {
-  const int lane = threadIdx.x & 31;
-  for (int round = 0; round < kTreeRounds; ++round) {
-    const int32_t ub = u0 + round * 32;
-    if (ub > r) break;
-    const int32_t u = ub + lane;
-    const bool valid = u <= r;
-    const int32_t j = virt_to_j<kBackward>(u, r);
-    const int p = valid ? (int)P[j] : 0;
-    const int maxp = __reduce_max_sync(0xffffffffu, valid ? p : 0);
-    const uint32_t lt = (1u << lane) - 1u;
-    int32_t M = -1, cnt = 0;
-    uint32_t myb = 0;
-    for (int v = 0; v <= maxp; ++v) {
-      const uint32_t b = __ballot_sync(0xffffffffu, valid && p == v);
-      if (lane == v) myb = b;
-      if (kApply) {
-        const int32_t cv = __shfl_sync(0xffffffffu, carry, v);
-        const uint32_t bl = b & lt;
-        const int32_t lastv = bl ? ub + 31 - __clz(bl) : cv;
-        if (v < p) {
-          if (v >= 1 && lastv > M) ++cnt;
-          M = max(M, lastv);
-        }
-      }
+constexpr uint32_t kNoPower = 0xFFu;  // staged power of a virtual index past r
+
+// Bytes P[b..b+3] as one little-endian word (bytes outside [0, r] read as kNoPower).  Reads
+// only the aligned words overlapping [0, r], which the P allocation covers whole.
+__device__ __forceinline__ uint32_t load_power_window(const uint8_t* __restrict__ P, int32_t r, int32_t b) {
+  const uint32_t* __restrict__ Pw = (const uint32_t*)P;
+  const int32_t wa = b >> 2;  // floor(b / 4), also for negative b
+  const uint32_t lo = (wa >= 0 && 4 * wa <= r) ? Pw[wa] : 0u;
+  const uint32_t hi = ((b & 3) != 0 && 4 * (wa + 1) <= r) ? Pw[wa + 1] : 0u;
+  uint32_t w = __funnelshift_r(lo, hi, (uint32_t)(b & 3) * 8u);
+  if (b < 0 || b + 3 > r) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      if (b + e < 0 || b + e > r) w |= kNoPower << (8 * e);
+  }
+  return w;
+}
+
+// Stage the powers of virtual indices [u0, u0 + kTreeTile) into sp (word k of the tile holds
+// virtual indices 4k..4k+3, stored at word k + k/8 so that a thread's chunk is 8 words and the
+// threads of a warp read distinct banks).
+template <bool kBackward>
+__device__ __forceinline__ void stage_tile_powers(const uint8_t* __restrict__ P, int32_t r, int32_t u0,
+                                                  uint32_t* __restrict__ sp) {
+  for (int k = threadIdx.x; k < kTreeTile / 4; k += kTreeThreads) {
+    uint32_t w;
+    if (!kBackward) {
+      w = load_power_window(P, r, u0 + 4 * k);
+    } else {
+      // virtual u0+4k+e is boundary r-u0-4k-e: the window starting 3 below, byte-reversed
+      w = __byte_perm(load_power_window(P, r, r - u0 - 4 * k - 3), 0u, 0x0123);
     }
-    if (kApply && valid && p >= 1) {
-      const int32_t nearest = virt_to_j<kBackward>(M, r);
-      near_out[j] = nearest;
-      if (kBackward)
-        depth_acc[j] = (uint8_t)(depth_acc[j] + cnt);
-      else
-        depth_acc[j] = (uint8_t)cnt;
+    sp[k + (k >> 3)] = w;
+  }
+}
+
+// Thread chunk pass: s_last[v][t] = last virtual index of power v in the thread's chunk (or -1).
+__device__ __forceinline__ void chunk_last(const uint32_t* __restrict__ sp, int32_t u0,
+                                           int32_t (*s_last)[kTreeThreads]) {
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int v = 0; v < 32; ++v) s_last[v][t] = -1;
+  const int32_t ub = u0 + t * kTreeChunk;
+#pragma unroll
+  for (int k = 0; k < kTreeChunk / 4; ++k) {
+    const uint32_t w = sp[t * 9 + k];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const uint32_t p = (w >> (8 * e)) & 0xFFu;
+      if (p != kNoPower) s_last[p & 31][t] = ub + 4 * k + e;
     }
-    if (myb) carry = ub + 31 - __clz(myb);
   }
 }
 
 template <bool kBackward>
-__global__ void __launch_bounds__(kTreeWarps * 32)
+__global__ void __launch_bounds__(kTreeThreads)
 tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr, int32_t* __restrict__ summary) {
-  __shared__ int32_t sw[kTreeWarps][32];
+  extern __shared__ __align__(16) uint8_t tsm[];
+  int32_t(*s_last)[kTreeThreads] = (int32_t(*)[kTreeThreads])tsm;
+  uint32_t* sp = (uint32_t*)(tsm + 32 * kTreeThreads * 4);
   const int32_t r = hdr->runs;
   const int32_t ntiles = r / kTreeTile + 1;  // virtual indices 0..r
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int32_t carry = -1;
-    tree_warp_rounds<kBackward, false>(P, r, t * kTreeTile + warp * kTreeRounds * 32, carry, nullptr, nullptr);
-    sw[warp][lane] = carry;
+  for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int32_t u0 = tile * kTreeTile;
+    stage_tile_powers<kBackward>(P, r, u0, sp);
     __syncthreads();
-    if (warp == 0) {
+    chunk_last(sp, u0, s_last);
+    __syncthreads();
+    // warp w reduces power values 4w..4w+3 over the tile's threads
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int v = warp * 4 + q;
       int32_t m = -1;
-      for (int w = 0; w < kTreeWarps; ++w) m = max(m, sw[w][lane]);
-      summary[t * 32 + lane] = m;
+#pragma unroll
+      for (int x = 0; x < kTreeThreads / 32; ++x) m = max(m, s_last[v][x * 32 + lane]);
+      m = __reduce_max_sync(0xffffffffu, m);
+      if (lane == 0) summary[tile * 32 + v] = m;
     }
     __syncthreads();
   }
@@ -160,26 +181,106 @@ tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__
   }
 }
 
+constexpr size_t kTreeSummarySmem = 32 * kTreeThreads * 4 + (kTreeTile / 4 + kTreeTile / 32) * 4;
+constexpr size_t kTreeApplySmem = kTreeSummarySmem + (size_t)(kTreeTile + kTreeTile / 32) * 4;
+
 template <bool kBackward>
-__global__ void __launch_bounds__(kTreeWarps * 32)
-tree_apply_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr,
-                  const int32_t* __restrict__ prefix, int32_t* __restrict__ near_out,
-                  uint8_t* __restrict__ depth_acc) {
-  __shared__ int32_t sw[kTreeWarps][32];
+__global__ void __launch_bounds__(kTreeThreads)
+tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, const int32_t* __restrict__ prefix,
+                  int32_t* __restrict__ near_out, uint8_t* __restrict__ depth_acc) {
+  extern __shared__ __align__(16) uint8_t tsm[];
+  int32_t(*s_last)[kTreeThreads] = (int32_t(*)[kTreeThreads])tsm;
+  uint32_t* sp = (uint32_t*)(tsm + 32 * kTreeThreads * 4);
+  int32_t* s_near = (int32_t*)(tsm + kTreeSummarySmem);  // index i stored at i + i/32
   const int32_t r = hdr->runs;
   const int32_t ntiles = r / kTreeTile + 1;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int32_t u0 = t * kTreeTile + warp * kTreeRounds * 32;
-    int32_t c = -1;
-    tree_warp_rounds<kBackward, false>(P, r, u0, c, nullptr, nullptr);
-    sw[warp][lane] = c;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  bool bad = false;
+  for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int32_t u0 = tile * kTreeTile;
+    stage_tile_powers<kBackward>(P, r, u0, sp);
     __syncthreads();
-    int32_t carry = prefix[t * 32 + lane];
-    for (int w = 0; w < warp; ++w) carry = max(carry, sw[w][lane]);
-    tree_warp_rounds<kBackward, true>(P, r, u0, carry, near_out, depth_acc);
+    chunk_last(sp, u0, s_last);
+    __syncthreads();
+    // exclusive max-scan of the chunk vectors over the tile's threads, after the tile prefix
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int v = warp * 4 + q;
+      int32_t carry = prefix[tile * 32 + v];
+#pragma unroll
+      for (int x = 0; x < kTreeThreads / 32; ++x) {
+        int32_t inc = s_last[v][x * 32 + lane];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+          const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+          if (lane >= d) inc = max(inc, o);
+        }
+        int32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
+        if (lane == 0) exc = -1;
+        s_last[v][x * 32 + lane] = max(carry, exc);
+        carry = max(carry, __shfl_sync(0xffffffffu, inc, 31));
+      }
+    }
+    __syncthreads();
+    // the stack in front of this thread's chunk
+    uint32_t occ = 0;
+    {
+      int32_t M = -1;
+#pragma unroll
+      for (int v = 0; v < 32; ++v) {
+        const int32_t x = s_last[v][t];
+        if (x > M) {
+          occ |= 1u << v;
+          M = x;
+        }
+      }
+    }
+    // walk the chunk: nearest smaller on this side and the number of stack entries of power >= 1;
+    // the count byte replaces the staged power (0xFF: no node here)
+    const int32_t ub = u0 + t * kTreeChunk;
+#pragma unroll
+    for (int k = 0; k < kTreeChunk / 4; ++k) {
+      const uint32_t w = sp[t * 9 + k];
+      uint32_t cw = 0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const uint32_t p = (w >> (8 * e)) & 0xFFu;
+        const int32_t u = ub + 4 * k + e;
+        const int i = t * kTreeChunk + 4 * k + e;
+        uint32_t cnt = 0xFFu;
+        if (p == 0) {
+          occ = 1u;
+          s_last[0][t] = u;
+        } else if (p != kNoPower) {
+          const uint32_t pp = p & 31u;
+          const uint32_t om = occ & ((1u << pp) - 1u);
+          if (om == 0u) bad = true;  // the power-0 sentinel is always below
+          const int top = om ? 31 - __clz(om) : 0;
+          s_near[i + (i >> 5)] = s_last[top][t];
+          cnt = (uint32_t)__popc(om) - 1u;
+          occ = om | (1u << pp);
+          s_last[pp][t] = u;
+        }
+        cw |= cnt << (8 * e);
+      }
+      sp[t * 9 + k] = cw;
+    }
+    __syncthreads();
+    // coalesced write-out
+    for (int i = t; i < kTreeTile; i += kTreeThreads) {
+      const int32_t u = u0 + i;
+      if (u > r) break;
+      const uint32_t cnt = (sp[(i >> 2) + (i >> 5)] >> (8 * (i & 3))) & 0xFFu;
+      if (cnt != 0xFFu) {
+        const int32_t j = virt_to_j<kBackward>(u, r);
+        near_out[j] = virt_to_j<kBackward>(s_near[i + (i >> 5)], r);
+        if (kBackward) depth_acc[j] = (uint8_t)(depth_acc[j] + cnt);
+        else depth_acc[j] = (uint8_t)cnt;
+      }
+    }
     __syncthreads();
   }
+  if (bad) post_status(&hdr->status, nullptr, kDevInternal);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -343,12 +444,21 @@ static int persistent_blocks(int per_sm) {
 cudaError_t launch_meta_stages(const Ctx& c) {
   const int grid = persistent_blocks(8);
   node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
-  tree_summary_kernel<false><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_sum);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tree_apply_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeApplySmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(tree_apply_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTreeApplySmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int tgrid = persistent_blocks(4);
+  tree_summary_kernel<false><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum);
   tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
-  tree_apply_kernel<false><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeL, c.ndepth);
-  tree_summary_kernel<true><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_sum);
+  tree_apply_kernel<false><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeL, c.ndepth);
+  tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum);
   tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
-  tree_apply_kernel<true><<<grid, kTreeWarps * 32, 0, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeR, c.ndepth);
+  tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                           c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.hdr);
