@@ -59,6 +59,7 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.thr_F = segmented ? (uint64_t*)take(dthreads * 8) : nullptr;
   c.thr_fn = (uint32_t*)take(dthreads * 4);
   const size_t tree_tiles = (size_t)(n + 1) / kTreeTile + 1;
+  c.tree_stride = (int32_t)tree_tiles;
   c.tree_sum = (int32_t*)take(tree_tiles * 32 * 4);
   c.tree_pre = (int32_t*)take(tree_tiles * 32 * 4);
   c.sub_lim = sub_tile((int)kb);

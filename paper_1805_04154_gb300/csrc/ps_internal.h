@@ -37,7 +37,8 @@ struct Ctx {
   uint64_t* thr_L = nullptr;    // per detection thread: pair bits of its 32 positions
   uint64_t* thr_F = nullptr;    // forced-start bits (segmented calls only)
   uint32_t* thr_fn = nullptr;   // its transition function with run counts
-  int32_t* tree_sum = nullptr;  // [tree tiles][32]
+  int32_t* tree_sum = nullptr;  // [32 power values][tree_stride tiles]
+  int32_t tree_stride = 0;
   int32_t* tree_pre = nullptr;
 
   int32_t sub_lim = 0;          // subtree-in-SMEM element limit

@@ -14,28 +14,43 @@ namespace ps {
 // the power is the number of leading zeros of x ^ y in 32 bits.  Boundaries between segments
 // and the sentinels j = 0, j = r get power 0 (smaller than every real power).
 // ---------------------------------------------------------------------------------------
+// floor(a / d) for a < 2^63 and 2 <= d < 2^33, given m = floor((2^64 - 1) / d): division by an
+// invariant integer through a multiply-high (Granlund and Montgomery, PLDI 1994).  Because
+// a m / 2^64 lies in (a/d - 3/4, a/d], the estimate is q or q - 1, fixed by one remainder test.
+__device__ __forceinline__ uint64_t div_invariant(uint64_t a, uint64_t d, uint64_t m) {
+  uint64_t q = __umul64hi(a, m);
+  if (a - q * d >= d) ++q;
+  return q;
+}
+
 __global__ void node_power_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ run_seg,
                                   const int64_t* __restrict__ offsets, int32_t n, uint8_t* __restrict__ P,
                                   const PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
+  int32_t cached_seg = -1;
+  int64_t base = 0, ns = n;
+  uint64_t two_n = 2 * (uint64_t)n, m = ~0ull / (2 * (uint64_t)max(n, 1));
   for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= r; j += gridDim.x * blockDim.x) {
     uint8_t p = 0;
     if (j >= 1 && j < r) {
-      int64_t base = 0, ns = n;
       bool same = true;
       if (run_seg != nullptr) {
         const int32_t sg = run_seg[j];
         same = (run_seg[j - 1] == sg);
-        base = offsets[sg];
-        ns = offsets[sg + 1] - base;
+        if (same && sg != cached_seg) {
+          cached_seg = sg;
+          base = offsets[sg];
+          ns = offsets[sg + 1] - base;
+          two_n = 2 * (uint64_t)(ns > 0 ? ns : 1);
+          m = ~0ull / two_n;
+        }
         if (ns <= 0) same = false;  // only with invalid offsets, which the host rejects
       }
       if (same) {
         const uint64_t l2 = (uint64_t)((int64_t)S[j - 1] + S[j] - 2 * base);
         const uint64_t r2 = (uint64_t)((int64_t)S[j] + S[j + 1] - 2 * base);
-        const uint64_t two_n = (uint64_t)(2 * ns);
-        const uint32_t x = (uint32_t)((l2 << 31) / two_n);
-        const uint32_t y = (uint32_t)((r2 << 31) / two_n);
+        const uint32_t x = (uint32_t)div_invariant(l2 << 31, two_n, m);
+        const uint32_t y = (uint32_t)div_invariant(r2 << 31, two_n, m);
         p = (uint8_t)min(__clz(x ^ y), 31);
       }
     }
@@ -123,7 +138,8 @@ __device__ __forceinline__ void chunk_last(const uint32_t* __restrict__ sp, int3
 
 template <bool kBackward>
 __global__ void __launch_bounds__(kTreeThreads)
-tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr, int32_t* __restrict__ summary) {
+tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict__ hdr, int32_t* __restrict__ summary,
+                    int32_t stride) {
   extern __shared__ __align__(16) uint8_t tsm[];
   int32_t(*s_last)[kTreeThreads] = (int32_t(*)[kTreeThreads])tsm;
   uint32_t* sp = (uint32_t*)(tsm + 32 * kTreeThreads * 4);
@@ -144,28 +160,33 @@ tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict_
 #pragma unroll
       for (int x = 0; x < kTreeThreads / 32; ++x) m = max(m, s_last[v][x * 32 + lane]);
       m = __reduce_max_sync(0xffffffffu, m);
-      if (lane == 0) summary[tile * 32 + v] = m;
+      if (lane == 0) summary[v * stride + tile] = m;
     }
     __syncthreads();
   }
 }
 
-// exclusive max-scan over tiles, one warp per power value (grid: 1 block of 32 warps)
+// exclusive max-scan over tiles, one warp per power value (grid: 1 block of 32 warps); the
+// summaries are stored power-major, so each warp reads consecutive tiles
 __global__ void __launch_bounds__(1024)
-tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__ summary, int32_t* __restrict__ prefix) {
+tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__ summary, int32_t* __restrict__ prefix,
+                 int32_t stride) {
+  constexpr int kPer = 16;  // loads in flight per lane
   const int32_t r = hdr->runs;
   const int32_t ntiles = r / kTreeTile + 1;
   const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int32_t* __restrict__ in = summary + (size_t)v * stride;
+  int32_t* __restrict__ out = prefix + (size_t)v * stride;
   int32_t run = -1;
-  for (int32_t base = 0; base < ntiles; base += 32 * 4) {
-    int32_t x[4];
+  for (int32_t base = 0; base < ntiles; base += 32 * kPer) {
+    int32_t x[kPer];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kPer; ++q) {
       const int32_t t = base + q * 32 + lane;
-      x[q] = t < ntiles ? summary[t * 32 + v] : -1;
+      x[q] = t < ntiles ? in[t] : -1;
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kPer; ++q) {
       int32_t inc = x[q];
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -175,7 +196,7 @@ tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__
       int32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
       if (lane == 0) exc = -1;
       const int32_t t = base + q * 32 + lane;
-      if (t < ntiles) prefix[t * 32 + v] = max(run, exc);
+      if (t < ntiles) out[t] = max(run, exc);
       run = max(run, __shfl_sync(0xffffffffu, inc, 31));
     }
   }
@@ -187,7 +208,7 @@ constexpr size_t kTreeApplySmem = kTreeSummarySmem + (size_t)(kTreeTile + kTreeT
 template <bool kBackward>
 __global__ void __launch_bounds__(kTreeThreads)
 tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, const int32_t* __restrict__ prefix,
-                  int32_t* __restrict__ near_out, uint8_t* __restrict__ depth_acc) {
+                  int32_t stride, int32_t* __restrict__ near_out, uint8_t* __restrict__ depth_acc) {
   extern __shared__ __align__(16) uint8_t tsm[];
   int32_t(*s_last)[kTreeThreads] = (int32_t(*)[kTreeThreads])tsm;
   uint32_t* sp = (uint32_t*)(tsm + 32 * kTreeThreads * 4);
@@ -206,7 +227,7 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int v = warp * 4 + q;
-      int32_t carry = prefix[tile * 32 + v];
+      int32_t carry = prefix[v * stride + tile];
 #pragma unroll
       for (int x = 0; x < kTreeThreads / 32; ++x) {
         int32_t inc = s_last[v][x * 32 + lane];
@@ -453,12 +474,12 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     attr = true;
   }
   const int tgrid = persistent_blocks(4);
-  tree_summary_kernel<false><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum);
-  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
-  tree_apply_kernel<false><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeL, c.ndepth);
-  tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum);
-  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre);
-  tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.nodeR, c.ndepth);
+  tree_summary_kernel<false><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
+  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
+  tree_apply_kernel<false><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeL, c.ndepth);
+  tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
+  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
+  tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                           c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.hdr);
