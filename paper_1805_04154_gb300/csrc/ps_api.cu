@@ -31,8 +31,12 @@ const KeyLaunch* launch_for(int kt) {
 
 int key_bytes(int kt) { return kt == PS_KEY_U64 ? 8 : 4; }
 
+// Chunk-boundary slots of one fused pass: per node floor(size / kChunkSpan) + 2, for at most
+// `cap` nodes (those larger than the subtree limit).
+size_t chunk_capacity(int64_t n, size_t cap) { return (size_t)n / kChunkSpan + 2 * cap + 64; }
+
 // Carve the workspace into the per-call arrays.  With base == nullptr only the size is computed.
-size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented) {
+size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented, bool fused) {
   size_t cur = 0;
   auto take = [&](size_t bytes) -> void* {
     cur = (cur + 255) & ~(size_t)255;
@@ -65,6 +69,13 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.sub_lim = sub_tile((int)kb);
   c.small_tasks = (int32_t*)take(N * 4);
   const size_t cap = (size_t)n / (size_t)(c.sub_lim + 1) + 2;
+  if (fused) {
+    c.lsplit = (int32_t*)take(N * 4);
+    c.rsplit = (int32_t*)take(N * 4);
+    c.chunk_tab = (int4*)take(chunk_capacity(n, cap) * sizeof(int4));
+    c.item_ext = (int4*)take(cap * sizeof(int4));
+  }
+  c.fused = fused;
   c.leaf_items = (int32_t*)take(cap * 4);
   c.leaf_tile_off = (uint32_t*)take(cap * 4);
   c.level_cap = (int32_t)cap;
@@ -174,6 +185,16 @@ int pass_stages_setting() {
   return v;
 }
 
+// Fused passes (two tree levels per HBM pass) unless PS_FUSED=0 selects binary passes.
+bool fused_setting() {
+  static int v = -1;
+  if (v < 0) {
+    const char* e = std::getenv("PS_FUSED");
+    v = (e && e[0] == '0') ? 0 : 1;
+  }
+  return v != 0;
+}
+
 ps_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return PS_OK;
   if (e == cudaErrorMemoryAllocation) return PS_ERR_OUT_OF_MEMORY;
@@ -214,7 +235,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     return PS_OK;
   }
   Ctx c;
-  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented);
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, fused_setting());
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
   int dev = 0;
   PS_TRY(cudaGetDevice(&dev));
@@ -304,7 +325,13 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
     if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
-    {
+    if (c.fused) {
+      // fused passes exist at even depths only; tiles counts chunk-boundary slots
+      if ((d & 1) || (uint64_t)tiles > chunk_capacity(n, (size_t)c.level_cap)) return PS_ERR_INTERNAL;
+      StageTimer t(5, s);
+      PS_TRY(kl->fused_merge(c, d, items, tiles));
+      t.done(2 * h.level_elems[d] * eb, 2);
+    } else {
       StageTimer t(5, s);
       PS_TRY(kl->merge(c, d, items, tiles));
       t.done(2 * h.level_elems[d] * eb, 1);
@@ -323,7 +350,7 @@ ps_status with_pool(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   cudaMemPool_t pool = lib_pool(dev);
   if (!pool) return PS_ERR_CUDA;
   Ctx tmp;
-  const size_t bytes = carve(tmp, nullptr, kt, vals != nullptr, n, segmented);
+  const size_t bytes = carve(tmp, nullptr, kt, vals != nullptr, n, segmented, fused_setting());
   void* ws = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&ws, bytes, pool, s);
   if (e != cudaSuccess) return PS_ERR_OUT_OF_MEMORY;
@@ -392,7 +419,7 @@ extern "C" {
 size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented) {
   if (!launch_for(key_type) || n < 0) return 0;
   Ctx c;
-  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0);
+  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0, fused_setting());
 }
 
 ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,
@@ -495,7 +522,7 @@ ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_i
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals_in ? up((size_t)n * 4 + 16) : 0;
   Ctx tmp;
-  const size_t wbytes = carve(tmp, nullptr, key_type, vals_in != nullptr, n, false);
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals_in != nullptr, n, false, fused_setting());
   uint8_t* base = nullptr;
   if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
     return PS_ERR_OUT_OF_MEMORY;
@@ -625,7 +652,7 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   uint8_t* scratch = noalloc_scratch(dev);
   if (!scratch) return PS_ERR_CUDA;
   Ctx c;
-  const size_t need = carve(c, scratch, kt, vals != nullptr, n, false);
+  const size_t need = carve(c, scratch, kt, vals != nullptr, n, false, false);
   if (need + 256 > kNoAllocScratchBytes) return PS_ERR_INTERNAL;
   c.stream = s;
   c.kt = kt;

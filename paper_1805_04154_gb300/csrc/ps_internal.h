@@ -43,6 +43,11 @@ struct Ctx {
 
   int32_t sub_lim = 0;          // subtree-in-SMEM element limit
   int pass_stages = 2;          // shared-memory stages of the level-pass ring (2, 3, 4 or 6)
+  bool fused = false;           // fused passes (two tree levels per HBM pass) or binary passes
+  int32_t* lsplit = nullptr;    // fused: split position of a node's left child of odd depth
+  int32_t* rsplit = nullptr;    //        ... and of its right child
+  int4* chunk_tab = nullptr;    // fused: chunk boundaries of the current pass (c1, c2, c3, c4)
+  int4* item_ext = nullptr;     // fused: per item of the current pass (s1, s2, samples, 0)
   int32_t* small_tasks = nullptr;
   int32_t* leaf_items = nullptr;
   uint32_t* leaf_tile_off = nullptr;
@@ -61,6 +66,7 @@ struct KeyLaunch {
   cudaError_t (*small)(const Ctx&, uint32_t ntasks);
   cudaError_t (*place)(const Ctx&, uint32_t nitems, uint32_t ntiles);
   cudaError_t (*merge)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
+  cudaError_t (*fused_merge)(const Ctx&, int depth, uint32_t nitems, uint32_t nslots);
 };
 extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
 

@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-               const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+               const int32_t* __restrict__ tasks, int fused, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
   typedef typename K::T T;
   typedef SubElem<K> E;
   typedef typename E::R R;
@@ -375,8 +375,8 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
     __syncthreads();
   }
 
-  // 5. write-out: the subtree root belongs in global buffer droot mod 2
-  const bool odd = (droot & 1) != 0;  // (selects, not an indexed parameter array: no local copy)
+  // 5. write-out into the buffer that holds the subtree root's output (out_buffer)
+  const bool odd = out_buffer(droot, fused != 0) == 1;  // selects, not an indexed parameter array
   T* __restrict__ ok = (T*)(odd ? buf.k[1] : buf.k[0]);
   if (V) {
     uint32_t* pay = (uint32_t*)meta;  // the node list is no longer needed
@@ -417,14 +417,15 @@ __device__ __forceinline__ int32_t slot_of_tile(const uint32_t* __restrict__ til
 }
 
 // ---------------------------------------------------------------------------------------
-// Large leaves: odd depth -> scratch buffer (reversed if descending); even depth and
-// descending -> reversed in place.  One CTA per kMergeTile outputs (or pairs).
+// Large leaves whose depth maps to the scratch buffer -> copied there (reversed if
+// descending); the others, if descending -> reversed in place.  One CTA per kMergeTile outputs
+// (or pairs).
 // ---------------------------------------------------------------------------------------
 template <class K, bool V>
 __global__ void __launch_bounds__(256)
 leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                   const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                  const uint32_t* __restrict__ tile_off, uint32_t nitems) {
+                  const uint32_t* __restrict__ tile_off, uint32_t nitems, int fused) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
   __shared__ int32_t s_slot;
@@ -440,7 +441,7 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
   // all loads of the thread first (independent, coalesced even when reversed), then the stores
   T kx[kPer], ky[kPer];
   uint32_t vx[kPer], vy[kPer];
-  if (ldepth[i] & 1) {
+  if (out_buffer(ldepth[i], fused != 0) == 1) {
     T* __restrict__ k1 = (T*)buf.k[1];
     uint32_t* __restrict__ v1 = buf.v[1];
     const int32_t q0 = s + k * kMergeTile + threadIdx.x, q1 = min(e, s + (k + 1) * kMergeTile);

@@ -313,8 +313,12 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
 //  * larger leaves that must move (odd depth -> scratch buffer, or descending -> reversed) get
 //    placement tiles;
 //  * larger internal nodes are merged by HBM passes, one pass per depth.
-// Buffer parity: a node at depth d writes buffer d mod 2 (0 = the caller's arrays) and reads
-// its children from buffer (d+1) mod 2, so every leaf starts in buffer (depth mod 2).
+// Buffer parity (out_buffer): with binary passes a node at depth d writes buffer d mod 2 (0 =
+// the caller's arrays) and reads its children from buffer (d+1) mod 2, so every leaf starts in
+// buffer (depth mod 2).  With fused passes only nodes of even depth are written by HBM passes;
+// a large node of odd depth is merged inside its parent's pass (the parent learns its split
+// position through lsplit / rsplit), and everything materialised at depth d sits in buffer
+// ceil(d / 2) mod 2.
 // M = sum over leaves of depth x length (Sec. 2.3).
 // ---------------------------------------------------------------------------------------
 __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
@@ -323,7 +327,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
                             uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
                             int4* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
-                            int32_t level_cap, int32_t small_cap, PlanHeader* __restrict__ hdr) {
+                            int32_t level_cap, int32_t small_cap, int fused, int32_t* __restrict__ lsplit,
+                            int32_t* __restrict__ rsplit, PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   unsigned long long cost = 0;
   int32_t maxd = 0;
@@ -354,7 +359,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
       } else {
         const bool desc = run_desc[x] != 0;
         uint32_t tiles = 0;
-        if (d & 1) tiles = (uint32_t)((len + kMergeTile - 1) / kMergeTile);
+        const bool odd_buf = out_buffer(d, fused != 0) == 1;
+        if (odd_buf) tiles = (uint32_t)((len + kMergeTile - 1) / kMergeTile);
         else if (desc) tiles = (uint32_t)((len / 2 + kMergeTile - 1) / kMergeTile);
         if (tiles) {
           const unsigned long long old = atomicAdd(&hdr->leaf_ctr, (1ull << 32) | tiles);
@@ -362,7 +368,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           if (slot < (uint32_t)level_cap) {
             leaf_items[slot] = x;
             leaf_tile_off[slot] = (uint32_t)(old & 0xffffffffu);
-            atomicAdd(&hdr->place_elems, (unsigned long long)((d & 1) ? len : 2 * (len / 2)));
+            atomicAdd(&hdr->place_elems, (unsigned long long)(odd_buf ? len : 2 * (len / 2)));
           } else {
             post_status(&hdr->status, nullptr, kDevInternal);
           }
@@ -383,9 +389,16 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         }
       } else {
         const int d = ndepth[x];
-        const uint32_t tiles = (uint32_t)((hi - 1) / kMergeTile - lo / kMergeTile + 1);
+        // binary passes: output tiles of kMergeTile; fused passes: chunk-boundary slots
+        const uint32_t tiles = fused ? (uint32_t)(size / kChunkSpan + 2)
+                                     : (uint32_t)((hi - 1) / kMergeTile - lo / kMergeTile + 1);
         if (d >= kMaxLevels) {
           post_status(&hdr->status, nullptr, kDevInternal);
+        } else if (fused && (d & 1)) {
+          // odd depth: merged inside the fused pass of its parent; record where it splits
+          if (par < 0) post_status(&hdr->status, nullptr, kDevInternal);
+          else if (par == nodeR[x]) lsplit[par] = S[x];  // x is the left child of nodeR[x]
+          else rsplit[par] = S[x];
         } else {
           const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
@@ -482,7 +495,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
-                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.hdr);
+                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
+                                          c.lsplit, c.rsplit, c.hdr);
   return cudaGetLastError();
 }
 
