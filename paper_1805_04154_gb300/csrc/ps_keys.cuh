@@ -120,7 +120,7 @@ struct Launch {
     // the pass at (even) depth d reads what depths d+1 and d+2 left in their buffer
     const int src = out_buffer(depth + 1, true), dst = out_buffer(depth, true);
     const size_t off = (size_t)depth * c.level_cap;
-    const uint32_t tgrid = (uint32_t)std::min<uint64_t>((nslots + 255) / 256, (uint64_t)sms * 8);
+    const uint32_t tgrid = (uint32_t)std::min<uint64_t>((nslots + 63) / 64, (uint64_t)sms * 8);  // 4 threads per slot
     chunk_table_kernel<K><<<tgrid, 256, 0, c.stream>>>((const T*)c.k[src], c.level_items + off,
                                                       c.level_tile_off + off, nitems, nslots, c.nodeL, c.nodeR,
                                                       c.lsplit, c.rsplit, c.sub_lim, c.chunk_tab, c.item_ext,
