@@ -130,6 +130,35 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
                      uint8_t* leaf_depth, int32_t* node_left, int32_t* node_right,
                      uint8_t* node_depth, void* stream);
 
+/* Merge tree.  PS_TREE_POWERSORT: Alg. 2's tree, the Cartesian tree of the node powers (the
+ * default of every other entry point).  PS_TREE_PEEKSORT: Alg. 1's tree, Mehlhorn's Method 1 on
+ * the run lengths (Peeksort theorem): a range of runs is split at the run boundary nearest its
+ * middle position (after its first run if the middle lies in it, before its last run if the
+ * middle lies in that, else at the nearer end of the run holding the middle), applied to the
+ * same greedy runs.  Both produce the same (unique stable) output; they differ in the merges
+ * and hence the merge cost M. */
+typedef enum { PS_TREE_POWERSORT = 0, PS_TREE_PEEKSORT = 1 } ps_tree;
+
+/* ps_workspace_size for the given merge tree (PS_TREE_PEEKSORT needs 8 (n + 2) bytes more for
+ * the level-by-level tree construction).  0 for an unknown key type or tree. */
+size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segmented, int tree);
+
+/* ps_sort_ws (d_offsets NULL, count 1) or ps_sort_segmented_ws (d_offsets non-NULL) with the
+ * merge tree chosen by `tree`; workspace of ps_workspace_size_tree(..., tree) bytes.  Errors as
+ * for those entry points, plus PS_ERR_INVALID_ARG for an unknown tree and PS_ERR_INTERNAL if a
+ * peeksort tree were deeper than the plan's 32 levels. */
+ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                          int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ps_analyze with the merge tree chosen by `tree`.  For PS_TREE_PEEKSORT, power[j] receives the
+ * node's depth + 1 at every internal boundary (0 at sentinels and segment borders): the order in
+ * which the plan finds parents (a leaf's parent is the larger of its two boundaries, a node's
+ * parent the larger of its range ends), as node powers do for Alg. 2. */
+ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
+                          int tree, void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
+                          int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                          int32_t* node_right, uint8_t* node_depth, void* stream);
+
 /* Plan statistics of one array (keys on the device, not modified; workspace from the pool).
  * Synchronizes the stream. */
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream);

@@ -21,12 +21,14 @@ __all__ = [
     "ps_sort", "ps_sort_ws", "ps_sort_segmented", "ps_sort_segmented_ws", "ps_workspace_size",
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
-    "ps_launch_count", "STAGES",
+    "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
+    "ps_sort_tree",
 ]
 
 STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
 
 PS_KEY_I32, PS_KEY_U32, PS_KEY_U64, PS_KEY_F32 = 0, 1, 2, 3
+PS_TREE_POWERSORT, PS_TREE_PEEKSORT = 0, 1
 _STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_ERR_OUT_OF_MEMORY",
            4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT", 6: "PS_ERR_INTERNAL"}
 
@@ -83,6 +85,10 @@ def load():
                 "ps_profile_enable": ([i32], i32),
                 "ps_profile_read": ([vp], i32),
                 "ps_launch_count": ([], u64),
+                "ps_workspace_size_tree": ([i32, i32, i64, i32, i32], sz),
+                "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+                "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                     vp], i32),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(lib, name)
@@ -132,8 +138,11 @@ def _dev_ptr(t: torch.Tensor | None, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def ps_workspace_size(key_type: int, has_vals: bool, n: int, segmented: bool = False) -> int:
-    return int(load().ps_workspace_size(key_type, 1 if has_vals else 0, n, 1 if segmented else 0))
+def ps_workspace_size(key_type: int, has_vals: bool, n: int, segmented: bool = False,
+                      tree: int = PS_TREE_POWERSORT) -> int:
+    if tree == PS_TREE_POWERSORT:
+        return int(load().ps_workspace_size(key_type, 1 if has_vals else 0, n, 1 if segmented else 0))
+    return int(load().ps_workspace_size_tree(key_type, 1 if has_vals else 0, n, 1 if segmented else 0, tree))
 
 
 def _workspace(nbytes: int, device) -> torch.Tensor:
@@ -171,6 +180,30 @@ def ps_sort(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: int 
     return keys
 
 
+def ps_sort_tree_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
+                    tree: int = PS_TREE_PEEKSORT, offsets: torch.Tensor | None = None,
+                    key_type: int | None = None, stream=None) -> None:
+    """ps_sort_ws / ps_sort_segmented_ws with the merge tree chosen by ``tree``."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
+        raise ValueError("vals must hold n 32-bit payloads")
+    seg = offsets is not None
+    _check(load().ps_sort_tree_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                                  _dev_ptr(offsets, "offsets") if seg else None,
+                                  (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(workspace, "workspace"),
+                                  workspace.numel(), _stream_ptr(stream, keys.device)), "ps_sort_tree_ws")
+
+
+def ps_sort_tree(keys: torch.Tensor, vals: torch.Tensor | None = None, tree: int = PS_TREE_PEEKSORT,
+                 offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> torch.Tensor:
+    """In-place stable sort with the merge tree chosen by ``tree`` (workspace from PyTorch)."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    ws = _workspace(ps_workspace_size(kt, vals is not None, keys.numel(), offsets is not None, tree), keys.device)
+    ps_sort_tree_ws(keys, vals, ws, tree, offsets, kt, stream)
+    return keys
+
+
 def ps_sort_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: torch.Tensor,
                       key_type: int | None = None, stream=None) -> torch.Tensor:
     """Sort every segment [offsets[k], offsets[k+1]) on its own (offsets: CUDA int64, count+1)."""
@@ -205,13 +238,14 @@ def ps_merge_cost(run_lengths) -> int:
 
 
 def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type: int | None = None,
-               stream=None) -> dict:
-    """Run detection, node powers and merge tree on the device (keys untouched); returns numpy
-    arrays: starts, desc, power, leaf_depth, node_left, node_right, node_depth, and runs, cost."""
+               stream=None, tree: int = PS_TREE_POWERSORT) -> dict:
+    """Run detection, node powers (or peeksort's tree) and merge tree on the device (keys
+    untouched); returns numpy arrays: starts, desc, power, leaf_depth, node_left, node_right,
+    node_depth, and runs, cost."""
     kt = key_type_of(keys) if key_type is None else key_type
     n = keys.numel()
     seg = offsets is not None
-    ws = _workspace(ps_workspace_size(kt, False, n, seg), keys.device)
+    ws = _workspace(ps_workspace_size(kt, False, n, seg, tree), keys.device)
     cap = n + 2
     out = {"starts": np.empty(cap, np.int32), "desc": np.empty(cap, np.uint8), "power": np.empty(cap, np.uint8),
            "leaf_depth": np.empty(cap, np.uint8), "node_left": np.empty(cap, np.int32),
@@ -219,11 +253,11 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
     runs = ctypes.c_int64(0)
     cost = ctypes.c_uint64(0)
     p = {k: ctypes.c_void_p(v.ctypes.data) for k, v in out.items()}
-    _check(load().ps_analyze(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
-                             (offsets.numel() - 1) if seg else 1, _dev_ptr(ws, "workspace"), ws.numel(),
-                             ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"], p["power"],
-                             p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
-                             _stream_ptr(stream, keys.device)), "ps_analyze")
+    _check(load().ps_analyze_tree(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
+                                  (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(ws, "workspace"),
+                                  ws.numel(), ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"],
+                                  p["power"], p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
+                                  _stream_ptr(stream, keys.device)), "ps_analyze")
     r = int(runs.value)
     res = {"runs": r, "cost": int(cost.value), "starts": out["starts"][: r + 1].copy(),
            "desc": out["desc"][:r].copy(), "power": out["power"][: r + 1].copy(),

@@ -36,7 +36,7 @@ int key_bytes(int kt) { return kt == PS_KEY_U64 ? 8 : 4; }
 size_t chunk_capacity(int64_t n, size_t cap) { return (size_t)n / kChunkSpan + 2 * cap + 64; }
 
 // Carve the workspace into the per-call arrays.  With base == nullptr only the size is computed.
-size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented, bool fused) {
+size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented, bool fused, int tree = 0) {
   size_t cur = 0;
   auto take = [&](size_t bytes) -> void* {
     cur = (cur + 255) & ~(size_t)255;
@@ -76,6 +76,14 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
     c.item_ext = (int4*)take(cap * sizeof(int4));
   }
   c.fused = fused;
+  c.tree = tree;
+  if (tree == PS_TREE_PEEKSORT) {
+    // ranges of one tree level: disjoint, each holding >= 2 runs, so at most (r + 1) / 2
+    c.peek_front_cap = (int32_t)(N / 2 + 2);
+    c.peek_front[0] = (int2*)take((size_t)c.peek_front_cap * sizeof(int2));
+    c.peek_front[1] = (int2*)take((size_t)c.peek_front_cap * sizeof(int2));
+    c.peek_count = (uint32_t*)take((kMaxLevels + 2) * sizeof(uint32_t));
+  }
   c.leaf_items = (int32_t*)take(cap * 4);
   c.leaf_tile_off = (uint32_t*)take(cap * 4);
   c.level_cap = (int32_t)cap;
@@ -221,9 +229,10 @@ ps_status check_args(int kt, const void* keys, const uint32_t* vals, int64_t n) 
 
 // The whole pipeline.  With `an` set, stops after planning and reports the plan instead.
 ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
-              bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an) {
+              bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an, int tree = 0) {
   ps_status st = check_args(kt, keys, vals, n);
   if (st != PS_OK) return st;
+  if (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT) return PS_ERR_INVALID_ARG;
   if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
   if (n == 0 || (n == 1 && !an)) {
     if (an) {
@@ -238,7 +247,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     return PS_OK;
   }
   Ctx c;
-  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, fused_setting());
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, fused_setting(), tree);
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
   int dev = 0;
   PS_TRY(cudaGetDevice(&dev));
@@ -266,7 +275,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   {
     StageTimer t(1, s);
     PS_TRY(launch_meta_stages(c));
-    t.done(0, 8);
+    t.done(0, (uint64_t)meta_launches(c));
   }
   if (an && an->stats) {
     PS_TRY(cudaMemsetAsync(c.d_entropy, 0, sizeof(double), s));
@@ -477,6 +486,29 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
   const bool seg = d_offsets != nullptr;
   return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
              workspace_bytes, (cudaStream_t)stream, &an);
+}
+
+size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segmented, int tree) {
+  if (!launch_for(key_type) || n < 0 || (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT)) return 0;
+  Ctx c;
+  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0, fused_setting(), tree);
+}
+
+ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                          int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream) {
+  const bool seg = d_offsets != nullptr;
+  return run(key_type, keys, vals, n, d_offsets, seg ? count : 1, seg, workspace, workspace_bytes,
+             (cudaStream_t)stream, nullptr, tree);
+}
+
+ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
+                          int tree, void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
+                          int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                          int32_t* node_right, uint8_t* node_depth, void* stream) {
+  AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
+  const bool seg = d_offsets != nullptr;
+  return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
+             workspace_bytes, (cudaStream_t)stream, &an, tree);
 }
 
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream) {

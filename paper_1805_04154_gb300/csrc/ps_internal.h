@@ -44,6 +44,10 @@ struct Ctx {
   int32_t sub_lim = 0;          // subtree-in-SMEM element limit
   int pass_stages = 2;          // shared-memory stages of the level-pass ring (2, 3, 4 or 6)
   bool fused = false;           // fused passes (two tree levels per HBM pass) or binary passes
+  int tree = 0;                 // merge tree: 0 powersort (Alg. 2), 1 peeksort (Alg. 1)
+  int2* peek_front[2] = {nullptr, nullptr};  // peeksort: run ranges of one tree level
+  uint32_t* peek_count = nullptr;            // peeksort: ranges per level [kMaxLevels + 1]
+  int32_t peek_front_cap = 0;
   int32_t* lsplit = nullptr;    // fused: split position of a node's left child of odd depth
   int32_t* rsplit = nullptr;    //        ... and of its right child
   int4* chunk_tab = nullptr;    // fused: chunk boundaries of the current pass (c1, c2, c3, c4)
@@ -72,6 +76,7 @@ extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
 
 // Key-independent stages (ps_meta.cu).
 cudaError_t launch_meta_stages(const Ctx& c);
+int meta_launches(const Ctx& c);
 cudaError_t launch_entropy(const Ctx& c, double* d_out);
 cudaError_t launch_check_offsets(const Ctx& c);
 

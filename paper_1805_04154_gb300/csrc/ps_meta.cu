@@ -305,6 +305,92 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
 }
 
 // ---------------------------------------------------------------------------------------
+// Peeksort's merge tree (Alg. 1; the Peeksort theorem: Mehlhorn's Method 1 on the run lengths).
+// A range of runs [a, b) with b - a >= 2, elements [l, r] (inclusive), is split at a run
+// boundary near its middle m = l + floor((r - l) / 2): after the first run if m lies in it,
+// before the last run if m lies in that, else at the nearer end of the run [i, j] containing m
+// (its start i if m - i < j - m, else after its end).  The tree is built level by level: each
+// range of the current level writes its node (the split boundary j: nodeL[j] = a,
+// nodeR[j] = b, depth) and appends its two sub-ranges that hold more than one run.  For the
+// plan, the boundary gets P[j] = depth + 1 (0 at sentinels and segment borders): a leaf's
+// parent is then the larger-P of its two boundaries and a node's parent the larger-P of its
+// range ends, the same rule as for node powers.
+// ---------------------------------------------------------------------------------------
+__global__ void peek_init_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ run_seg,
+                                 const int64_t* __restrict__ offsets, uint8_t* __restrict__ P,
+                                 int2* __restrict__ front0, uint32_t* __restrict__ count,
+                                 const PlanHeader* __restrict__ hdr) {
+  const int32_t r = hdr->runs;
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= r; j += gridDim.x * blockDim.x) {
+    P[j] = 0;
+    if (j == r) continue;
+    // one root per segment: the range of the segment's runs
+    if (run_seg == nullptr) {
+      if (j == 0 && r >= 2) {
+        front0[atomicAdd(&count[0], 1u)] = make_int2(0, r);
+      }
+    } else if (j == 0 || run_seg[j] != run_seg[j - 1]) {
+      const int64_t end = offsets[run_seg[j] + 1];
+      int32_t lo = j, hi = r;  // first run index at or past the segment's end
+      while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if ((int64_t)S[mid] < end) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo - j >= 2) front0[atomicAdd(&count[0], 1u)] = make_int2(j, lo);
+    }
+  }
+}
+
+__global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, const int2* __restrict__ cur,
+                                  int2* __restrict__ next, uint32_t* __restrict__ count, int32_t cap,
+                                  uint8_t* __restrict__ P, int32_t* __restrict__ nodeL, int32_t* __restrict__ nodeR,
+                                  uint8_t* __restrict__ ndepth, PlanHeader* __restrict__ hdr) {
+  const uint32_t m_cnt = count[level];
+  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < m_cnt; t += gridDim.x * blockDim.x) {
+    if (level >= kMaxLevels) {  // deeper than the plan's per-depth lists
+      post_status(&hdr->status, nullptr, kDevInternal);
+      return;
+    }
+    const int2 rg = cur[t];
+    const int32_t a = rg.x, b = rg.y;
+    const int64_t l = S[a], rr = (int64_t)S[b] - 1;
+    const int64_t e = (int64_t)S[a + 1] - 1, s = S[b - 1];
+    const int64_t m = l + (rr - l) / 2;
+    int32_t j;
+    if (m <= e) {
+      j = a + 1;
+    } else if (m >= s) {
+      j = b - 1;
+    } else {
+      int32_t lo = a + 1, hi = b - 1;  // run k containing m: largest k with S[k] <= m
+      while (hi - lo > 0) {
+        const int32_t mid = (lo + hi + 1) >> 1;
+        if ((int64_t)S[mid] <= m) lo = mid;
+        else hi = mid - 1;
+      }
+      const int64_t i = S[lo], jj = (int64_t)S[lo + 1] - 1;
+      j = (m - i < jj - m) ? lo : lo + 1;
+    }
+    nodeL[j] = a;
+    nodeR[j] = b;
+    ndepth[j] = (uint8_t)level;
+    P[j] = (uint8_t)(level + 1);
+    if (j - a >= 2 || b - j >= 2) {
+      const uint32_t add = (j - a >= 2 ? 1u : 0u) + (b - j >= 2 ? 1u : 0u);
+      const uint32_t at = atomicAdd(&count[level + 1], add);
+      if (at + add > (uint32_t)cap) {
+        post_status(&hdr->status, nullptr, kDevInternal);
+        continue;
+      }
+      uint32_t w = at;
+      if (j - a >= 2) next[w++] = make_int2(a, j);
+      if (b - j >= 2) next[w] = make_int2(j, b);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Planning.  Leaf i (run i) hangs below the adjacent boundary with the larger power (i or
 // i+1); its depth is that node's depth + 1, or 0 when the run is a whole segment.  Stage 4 is
 // organised around the element count sub_lim that one CTA can merge in shared memory:
@@ -475,8 +561,37 @@ static int persistent_blocks(int per_sm) {
   return sms * per_sm;
 }
 
+// Peeksort tree levels launched: one per node depth the plan can hold (0 .. kMaxLevels-1) plus
+// one more, whose ranges (a tree deeper than the plan's per-depth lists) post an internal error.
+// Launches past the tree's height find no ranges and return at once.
+static int peek_levels(int32_t) { return kMaxLevels + 1; }
+
+static cudaError_t launch_peek_tree(const Ctx& c) {
+  const int grid = persistent_blocks(8);
+  cudaError_t e = cudaMemsetAsync(c.peek_count, 0, (kMaxLevels + 1) * sizeof(uint32_t), c.stream);
+  if (e != cudaSuccess) return e;
+  peek_init_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.P, c.peek_front[0], c.peek_count, c.hdr);
+  const int levels = peek_levels(c.n);
+  for (int d = 0; d < levels; ++d)
+    peek_level_kernel<<<grid, 256, 0, c.stream>>>(c.S, d, c.peek_front[d & 1], c.peek_front[(d + 1) & 1],
+                                                  c.peek_count, c.peek_front_cap, c.P, c.nodeL, c.nodeR,
+                                                  c.ndepth, c.hdr);
+  return cudaGetLastError();
+}
+
+int meta_launches(const Ctx& c) { return c.tree == 1 ? 2 + peek_levels(c.n) : 8; }
+
 cudaError_t launch_meta_stages(const Ctx& c) {
   const int grid = persistent_blocks(8);
+  if (c.tree == 1) {
+    cudaError_t e = launch_peek_tree(c);
+    if (e != cudaSuccess) return e;
+    plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
+                                            c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
+                                            c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
+                                            c.lsplit, c.rsplit, c.hdr);
+    return cudaGetLastError();
+  }
   node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
   static bool attr = false;
   if (!attr) {

@@ -81,3 +81,11 @@ def test_merge_cost_host_matches_oracle(lib):
     bad = np.array([3, 0, 2], np.int64)
     assert lib.ps_merge_cost(ctypes.c_void_p(bad.ctypes.data), 3, ctypes.byref(out)) == 1
     assert lib.ps_merge_cost(None, 3, ctypes.byref(out)) == 1
+
+
+def test_tree_argument_errors_without_gpu(lib):
+    ws = ctypes.c_void_p(256)
+    # unknown merge tree: rejected before any CUDA call
+    assert lib.ps_sort_tree_ws(0, ctypes.c_void_p(4096), None, 10, None, 1, 7, ws, 1 << 20, None) == 1
+    assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 7) == 0
+    assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 1) > lib.ps_workspace_size_tree(0, 1, 1000, 0, 0)
