@@ -125,25 +125,33 @@ def _cpu_baseline(keys, vals, sample_desc: str):
             "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
 
 
-def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5):
-    """Sort throughput of one more workload (resident inputs, fresh copy per step)."""
+def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tree: int = 0):
+    """Sort throughput of one more workload (resident inputs, fresh copy per step); tree 1 uses
+    peeksort's merge tree (Alg. 1) instead of powersort's."""
     import numpy as np
     import torch
     eb = keys.dtype.itemsize + 4
     k0 = torch.from_numpy(keys.view({4: np.int32, 8: np.int64}[keys.dtype.itemsize])).to(dev)
     v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
-    an = ps.ps_analyze(k0, key_type=kt)
+    an = ps.ps_analyze(k0, key_type=kt, tree=tree)
     n = keys.size
-    ws = torch.empty(ps.ps_workspace_size(kt, True, n), dtype=torch.uint8, device=dev)
+    ws = torch.empty(ps.ps_workspace_size(kt, True, n, False, tree), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     copies = [(k0.clone(), v0.clone()) for _ in range(steps + 2)]
+
+    def one(i):
+        if tree:
+            ps.ps_sort_tree_ws(copies[i][0], copies[i][1], ws, tree, key_type=kt, stream=stream)
+        else:
+            ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
+
     for i in range(2):
-        ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
+        one(i)
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(2, steps + 2):
-        ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
+        one(i)
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
@@ -502,6 +510,10 @@ def run_gpu(args):
         del copies
         torch.cuda.empty_cache()
         var = []
+        hk, hv = _gen(n, SEED)
+        var.append(measure_variant(ps, dev, "peeksort merge tree (Alg. 1) on the headline workload", hk, hv, 0,
+                                   tree=1))
+        del hk, hv
         pk, pv = workloads.perm_i32(n, seed=SEED)
         var.append(measure_variant(ps, dev, f"random permutation, n={n} int32 + uint32 (runs ~2.4)", pk, pv, 0))
         del pk, pv
