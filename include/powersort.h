@@ -170,6 +170,20 @@ ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out
 ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
                        uint32_t* vals_out, int64_t n, void* stream);
 
+/* Host arrays sorted through caller-owned device memory, queued on `stream` without waiting for
+ * the result: copies keys_in/vals_in (host, n elements) into dev_keys/dev_vals (device, n
+ * elements, natural alignment), sorts them as ps_sort_ws does with `workspace`
+ * (ps_workspace_size(key_type, vals_in != NULL, n, 0) bytes), and copies the result to
+ * keys_out/vals_out (host; may alias the inputs).  The call returns once the sort's plan is
+ * known (one internal stream synchronization after the copy-in and planning); the copy-out is
+ * still in flight -- synchronize `stream` before reading keys_out.  With pinned host memory and
+ * one set of device buffers per stream, consecutive calls on different streams overlap the
+ * copy-in of one array, the sort of another and the copy-out of a third.  vals_in, vals_out and
+ * dev_vals are all NULL or all non-NULL.  Errors as for ps_sort_ws. */
+ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                          uint32_t* vals_out, int64_t n, void* dev_keys, uint32_t* dev_vals, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
 /* Measurement.  While enabled, every sort records CUDA events on its stream around its stages
  * (0 run detection, 1 node powers + merge tree + plan, 2 subtrees merged in shared memory,
  * 3 large-leaf placement, 4 unused, 5 level passes of the large merges).

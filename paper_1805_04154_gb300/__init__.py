@@ -22,7 +22,7 @@ __all__ = [
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
     "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
-    "ps_sort_tree",
+    "ps_sort_tree", "ps_sort_host_ws",
 ]
 
 STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
@@ -86,6 +86,7 @@ def load():
                 "ps_profile_read": ([vp], i32),
                 "ps_launch_count": ([], u64),
                 "ps_workspace_size_tree": ([i32, i32, i64, i32, i32], sz),
+                "ps_sort_host_ws": ([i32, vp, vp, vp, vp, i64, vp, vp, vp, sz, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
@@ -317,3 +318,16 @@ def ps_profile_read() -> dict:
 
 def ps_launch_count() -> int:
     return int(load().ps_launch_count())
+
+
+def ps_sort_host_ws(key_type: int, keys_in: int, vals_in: int | None, keys_out: int, vals_out: int | None, n: int,
+                    dev_keys: torch.Tensor, dev_vals: torch.Tensor | None, workspace: torch.Tensor,
+                    stream=None) -> None:
+    """Queue copy-in, sort and copy-out of host arrays (raw host pointers, pinned for asynchrony)
+    through caller-owned device buffers on ``stream``; synchronize the stream before reading the
+    output."""
+    _check(load().ps_sort_host_ws(key_type, ctypes.c_void_p(keys_in), ctypes.c_void_p(vals_in) if vals_in else None,
+                                  ctypes.c_void_p(keys_out), ctypes.c_void_p(vals_out) if vals_out else None, n,
+                                  _dev_ptr(dev_keys, "dev_keys"), _dev_ptr(dev_vals, "dev_vals"),
+                                  _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                  _stream_ptr(stream, dev_keys.device)), "ps_sort_host_ws")

@@ -227,6 +227,36 @@ ps_status check_args(int kt, const void* keys, const uint32_t* vals, int64_t n) 
   return PS_OK;
 }
 
+// Plan header read-back.  A kernel writes the header into a mapped pinned host buffer (one per
+// host thread and device) and the host waits on an event recorded after it.  A small
+// device-to-host copy would instead queue on the copy engine behind whatever large copies other
+// streams have in flight (e.g. the copy-out of the previous array in a pipelined caller).
+struct HeaderMailbox {
+  PlanHeader* host = nullptr;
+  PlanHeader* dev = nullptr;
+  cudaEvent_t ev = nullptr;
+  ~HeaderMailbox() {
+    if (ev) cudaEventDestroy(ev);
+    if (host) cudaFreeHost(host);
+  }
+};
+thread_local HeaderMailbox t_mailbox[kMaxDevices];
+
+ps_status read_plan_header(const Ctx& c, int dev, PlanHeader& h) {
+  if (dev < 0 || dev >= kMaxDevices) return PS_ERR_CUDA;
+  HeaderMailbox& m = t_mailbox[dev];
+  if (!m.host) {
+    PS_TRY(cudaHostAlloc((void**)&m.host, sizeof(PlanHeader), cudaHostAllocMapped));
+    PS_TRY(cudaHostGetDevicePointer((void**)&m.dev, m.host, 0));
+    PS_TRY(cudaEventCreateWithFlags(&m.ev, cudaEventDisableTiming));
+  }
+  PS_TRY(launch_header_out(c, m.dev));
+  PS_TRY(cudaEventRecord(m.ev, c.stream));
+  PS_TRY(cudaEventSynchronize(m.ev));
+  std::memcpy(&h, (const void*)m.host, sizeof(PlanHeader));
+  return PS_OK;
+}
+
 // The whole pipeline.  With `an` set, stops after planning and reports the plan instead.
 ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
               bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an, int tree = 0) {
@@ -283,8 +313,9 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     g_launches += 1;
   }
   PlanHeader h;
-  PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
-  PS_TRY(cudaStreamSynchronize(s));
+  st = read_plan_header(c, dev, h);
+  if (st != PS_OK) return st;
+  g_launches += 1;
   if (h.status & kDevBadOffsets) return PS_ERR_INVALID_ARG;
   if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
@@ -532,6 +563,26 @@ ps_status ps_stream_status(void* stream) {
     if (v & kDevTimeout) return PS_ERR_TIMEOUT;
     return PS_ERR_INTERNAL;
   }
+  return PS_OK;
+}
+
+ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
+                          uint32_t* vals_out, int64_t n, void* dev_keys, uint32_t* dev_vals, void* workspace,
+                          size_t workspace_bytes, void* stream) {
+  if (!launch_for(key_type) || n < 0) return PS_ERR_INVALID_ARG;
+  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n > 0 && (!keys_in || !keys_out || !dev_keys)) return PS_ERR_INVALID_ARG;
+  if ((vals_in == nullptr) != (vals_out == nullptr) || (vals_in != nullptr) != (dev_vals != nullptr))
+    return PS_ERR_INVALID_ARG;
+  if (n == 0) return PS_OK;
+  const size_t kb = (size_t)key_bytes(key_type);
+  cudaStream_t s = (cudaStream_t)stream;
+  PS_TRY(cudaMemcpyAsync(dev_keys, keys_in, (size_t)n * kb, cudaMemcpyHostToDevice, s));
+  if (dev_vals) PS_TRY(cudaMemcpyAsync(dev_vals, vals_in, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+  const ps_status st = run(key_type, dev_keys, dev_vals, n, nullptr, 1, false, workspace, workspace_bytes, s, nullptr);
+  if (st != PS_OK) return st;
+  PS_TRY(cudaMemcpyAsync(keys_out, dev_keys, (size_t)n * kb, cudaMemcpyDeviceToHost, s));
+  if (dev_vals) PS_TRY(cudaMemcpyAsync(vals_out, dev_vals, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
   return PS_OK;
 }
 

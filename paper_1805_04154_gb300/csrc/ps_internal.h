@@ -79,5 +79,6 @@ cudaError_t launch_meta_stages(const Ctx& c);
 int meta_launches(const Ctx& c);
 cudaError_t launch_entropy(const Ctx& c, double* d_out);
 cudaError_t launch_check_offsets(const Ctx& c);
+cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped);
 
 }  // namespace ps

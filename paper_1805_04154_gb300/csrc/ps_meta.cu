@@ -535,6 +535,16 @@ __global__ void entropy_kernel(const int32_t* __restrict__ S, const PlanHeader* 
   if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
 }
 
+// Plan header to a mapped host buffer (zero-copy): the host reads it after an event, without a
+// device-to-host copy that would queue behind large copies of other streams.
+__global__ void header_out_kernel(const PlanHeader* __restrict__ hdr, PlanHeader* out) {
+  static_assert(sizeof(PlanHeader) % 4 == 0, "header is whole words");
+  const uint32_t* src = (const uint32_t*)hdr;
+  volatile uint32_t* dst = (volatile uint32_t*)out;
+  for (int i = threadIdx.x; i < (int)(sizeof(PlanHeader) / 4); i += blockDim.x) dst[i] = src[i];
+  __threadfence_system();
+}
+
 // Segment offsets must start at 0, be non-decreasing and end at n.
 __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int32_t count, int64_t n,
                                      PlanHeader* __restrict__ hdr) {
@@ -617,6 +627,11 @@ cudaError_t launch_meta_stages(const Ctx& c) {
 
 cudaError_t launch_entropy(const Ctx& c, double* d_out) {
   entropy_kernel<<<persistent_blocks(4), 256, 0, c.stream>>>(c.S, c.hdr, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped) {
+  header_out_kernel<<<1, 128, 0, c.stream>>>(c.hdr, mapped);
   return cudaGetLastError();
 }
 

@@ -229,3 +229,27 @@ def test_unaligned_subarray_views(ps, kt, off):
     np.testing.assert_array_equal(hv[off:off + n], ref.vals)
     assert (hk[:off] == 0).all() and (hk[off + n:] == 0).all()
     assert (hv[:off] == 7).all() and (hv[off + n:] == 9).all()
+
+
+def test_host_ws_entry_on_streams(ps):
+    """ps_sort_host_ws: host arrays through caller-owned device buffers, three calls in flight on
+    three streams (copy-in, sort and copy-out of different arrays overlap); each result equals the
+    oracle's."""
+    inputs = [workloads.runs_i32(150001 + 7 * i, seed=40 + i) for i in range(3)]
+    refs = [oracle.powersort(k, v) for k, v in inputs]
+    streams = [torch.cuda.Stream() for _ in range(3)]
+    jobs = []
+    for (k, v), s in zip(inputs, streams):
+        n = k.size
+        hk, hv = torch.from_numpy(k).pin_memory(), torch.from_numpy(v.view(np.int32)).pin_memory()
+        ok_, ov = torch.empty_like(hk).pin_memory(), torch.empty_like(hv).pin_memory()
+        dk = torch.empty(n, dtype=torch.int32, device="cuda")
+        dv = torch.empty(n, dtype=torch.int32, device="cuda")
+        ws = torch.empty(ps.ps_workspace_size(0, True, n), dtype=torch.uint8, device="cuda")
+        ps.ps_sort_host_ws(0, hk.data_ptr(), hv.data_ptr(), ok_.data_ptr(), ov.data_ptr(), n, dk, dv, ws, stream=s)
+        jobs.append((hk, hv, ok_, ov, dk, dv, ws))
+    torch.cuda.synchronize()
+    assert ps.ps_stream_status() == 0
+    for (hk, hv, ok_, ov, *_), ref in zip(jobs, refs):
+        np.testing.assert_array_equal(ok_.numpy(), ref.keys)
+        np.testing.assert_array_equal(ov.numpy().view(np.uint32), ref.vals)
