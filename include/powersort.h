@@ -150,6 +150,19 @@ size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segment
 ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
                           int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Device-driven sort: as ps_sort_tree_ws (d_offsets NULL, count 1 for one array), but with no
+ * host round trip -- every launch after planning takes its work count from the plan on the
+ * device (persistent grids; one level-pass launch per depth the tree can have, empty ones return
+ * at once), so the call only queues work on `stream` and can be captured into a CUDA graph and
+ * replayed on the same buffers.  Binary level passes.  Argument errors are returned at once;
+ * errors found on the device (segment offsets, timeouts, internal) are reported by
+ * ps_stream_status, and with rejected offsets nothing is moved.  workspace:
+ * ps_workspace_size_tree(key_type, vals != NULL, n, d_offsets != NULL, tree) bytes.  The first
+ * call on a device allocates the library's status word and sets kernel attributes: make one
+ * call before capturing. */
+ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                           int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
+
 /* ps_analyze with the merge tree chosen by `tree`.  For PS_TREE_PEEKSORT, power[j] receives the
  * node's depth + 1 at every internal boundary (0 at sentinels and segment borders): the order in
  * which the plan finds parents (a leaf's parent is the larger of its two boundaries, a node's

@@ -22,7 +22,7 @@ __all__ = [
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
     "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
-    "ps_sort_tree", "ps_sort_host_ws",
+    "ps_sort_tree", "ps_sort_host_ws", "ps_sort_async_ws",
 ]
 
 STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
@@ -87,6 +87,7 @@ def load():
                 "ps_launch_count": ([], u64),
                 "ps_workspace_size_tree": ([i32, i32, i64, i32, i32], sz),
                 "ps_sort_host_ws": ([i32, vp, vp, vp, vp, i64, vp, vp, vp, sz, vp], i32),
+                "ps_sort_async_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
@@ -331,3 +332,19 @@ def ps_sort_host_ws(key_type: int, keys_in: int, vals_in: int | None, keys_out: 
                                   _dev_ptr(dev_keys, "dev_keys"), _dev_ptr(dev_vals, "dev_vals"),
                                   _dev_ptr(workspace, "workspace"), workspace.numel(),
                                   _stream_ptr(stream, dev_keys.device)), "ps_sort_host_ws")
+
+
+def ps_sort_async_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
+                     offsets: torch.Tensor | None = None, tree: int = PS_TREE_POWERSORT,
+                     key_type: int | None = None, stream=None) -> None:
+    """Device-driven sort (no host round trip; capturable into a CUDA graph).  Device-side
+    errors are reported by ``ps_stream_status``."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
+        raise ValueError("vals must hold n 32-bit payloads")
+    seg = offsets is not None
+    _check(load().ps_sort_async_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                                   _dev_ptr(offsets, "offsets") if seg else None,
+                                   (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(workspace, "workspace"),
+                                   workspace.numel(), _stream_ptr(stream, keys.device)), "ps_sort_async_ws")

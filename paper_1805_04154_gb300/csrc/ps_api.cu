@@ -383,6 +383,74 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   return PS_OK;
 }
 
+// Device-driven pipeline: no host round trip between planning and merging.  Every launch after
+// planning takes its work count from the plan header on the device (persistent grids; level
+// passes for every depth the tree can have, empty ones return at once), so the call only queues
+// work and can be captured into a CUDA graph.  Binary passes; errors found on the device reach
+// ps_stream_status, and with rejected segment offsets nothing is moved.
+ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
+                    bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, int tree) {
+  ps_status st = check_args(kt, keys, vals, n);
+  if (st != PS_OK) return st;
+  if (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT) return PS_ERR_INVALID_ARG;
+  if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
+  if (n <= 1) return PS_OK;
+  Ctx c;
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, false, tree);
+  if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  c.stream = s;
+  c.kt = kt;
+  c.key_bytes = key_bytes(kt);
+  c.has_vals = vals != nullptr;
+  c.n = (int32_t)n;
+  c.offsets = segmented ? d_offsets : nullptr;
+  c.count = segmented ? (int32_t)count : 1;
+  c.k[0] = keys;
+  c.v[0] = vals;
+  c.lib_status = lib_status_word(dev);
+  if (!c.lib_status) return PS_ERR_CUDA;
+  c.pass_stages = pass_stages_setting();
+  const KeyLaunch* kl = launch_for(kt);
+  // deepest node: depth < power <= floor(lg n) + 1 for Alg. 2; the plan's limit for Alg. 1
+  int maxd = kMaxLevels - 1;
+  if (tree == PS_TREE_POWERSORT) {
+    maxd = 0;
+    while (maxd < kMaxLevels - 1 && ((int64_t)1 << (maxd + 1)) <= n) ++maxd;
+  }
+  PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
+  {
+    StageTimer t(0, s);
+    if (segmented) PS_TRY(launch_check_offsets(c));
+    PS_TRY(kl->detect(c));
+    t.done(0, segmented ? 4 : 3);
+  }
+  {
+    StageTimer t(1, s);
+    PS_TRY(launch_meta_stages(c));
+    t.done(0, (uint64_t)meta_launches(c));
+  }
+  {
+    StageTimer t(2, s);
+    PS_TRY(kl->small(c, kCountOnDevice));
+    t.done(0, 1);
+  }
+  {
+    StageTimer t(3, s);
+    PS_TRY(kl->place(c, kCountOnDevice, kCountOnDevice));
+    t.done(0, 1);
+  }
+  {
+    StageTimer t(5, s);
+    for (int d = maxd; d >= 0; --d) PS_TRY(kl->merge(c, d, kCountOnDevice, kCountOnDevice));
+    t.done(0, (uint64_t)maxd + 1);
+  }
+  PS_TRY(launch_status_out(c));
+  g_launches += 1;
+  return PS_OK;
+}
+
 ps_status with_pool(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
                     bool segmented, cudaStream_t s, AnalyzeOut* an) {
   ps_status st = check_args(kt, keys, vals, n);
@@ -519,6 +587,13 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
              workspace_bytes, (cudaStream_t)stream, &an);
 }
 
+ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                           int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream) {
+  const bool seg = d_offsets != nullptr;
+  return run_async(key_type, keys, vals, n, d_offsets, seg ? count : 1, seg, workspace, workspace_bytes,
+                   (cudaStream_t)stream, tree);
+}
+
 size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segmented, int tree) {
   if (!launch_for(key_type) || n < 0 || (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT)) return 0;
   Ctx c;
@@ -560,6 +635,7 @@ ps_status ps_stream_status(void* stream) {
   if (cudaMemcpy(&v, w, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PS_ERR_CUDA;
   if (v) {
     if (cudaMemset(w, 0, 4) != cudaSuccess) return PS_ERR_CUDA;
+    if (v & kDevBadOffsets) return PS_ERR_INVALID_ARG;
     if (v & kDevTimeout) return PS_ERR_TIMEOUT;
     return PS_ERR_INTERNAL;
   }

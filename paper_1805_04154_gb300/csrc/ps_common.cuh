@@ -159,6 +159,9 @@ __device__ __forceinline__ void post_status(uint32_t* hdr_status, uint32_t* lib_
   if (lib_status) atomicOr(lib_status, bits);
 }
 
+// Launch-argument sentinel: take the work count from the plan header on the device.
+constexpr uint32_t kCountOnDevice = 0xFFFFFFFFu;
+
 // Bounded waits: iterations before a wait gives up and posts kDevTimeout.  Look-back polls
 // sleep 64 ns between reads (about 0.3 s in all); an mbarrier try_wait suspends for a
 // hardware-defined interval per call.

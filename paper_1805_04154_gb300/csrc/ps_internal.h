@@ -80,5 +80,6 @@ int meta_launches(const Ctx& c);
 cudaError_t launch_entropy(const Ctx& c, double* d_out);
 cudaError_t launch_check_offsets(const Ctx& c);
 cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped);
+cudaError_t launch_status_out(const Ctx& c);
 
 }  // namespace ps

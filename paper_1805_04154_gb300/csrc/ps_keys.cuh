@@ -26,6 +26,18 @@ struct Launch {
     return cudaGetLastError();
   }
 
+  static int sm_count() {
+    static int sms = 0;
+    if (sms == 0) {
+      int dev = 0;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (sms <= 0) sms = 152;
+    }
+    return sms;
+  }
+
+  // ntasks == kCountOnDevice: persistent grid, the count is read from the plan on the device
   template <bool V>
   static cudaError_t small_v(const Ctx& c, uint32_t ntasks) {
     static bool attr = false;
@@ -37,9 +49,11 @@ struct Launch {
       attr = true;
     }
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
-    subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
-                                                                    c.ndepth, c.ldepth, c.small_tasks,
-                                                                    c.fused ? 1 : 0, c.hdr, c.lib_status);
+    const uint32_t grid = ntasks == kCountOnDevice ? (uint32_t)sm_count() * 4 : ntasks;
+    subtree_kernel<K, V><<<grid, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth,
+                                                                  c.ldepth, c.small_tasks, ntasks,
+                                                                  (uint32_t)(c.n + 2), c.fused ? 1 : 0, c.hdr,
+                                                                  c.lib_status);
     return cudaGetLastError();
   }
   static cudaError_t small(const Ctx& c, uint32_t ntasks) {
@@ -50,12 +64,16 @@ struct Launch {
   static cudaError_t place(const Ctx& c, uint32_t nitems, uint32_t ntiles) {
     if (ntiles == 0) return cudaSuccess;
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
+    const uint32_t grid = ntiles == kCountOnDevice ? (uint32_t)sm_count() * 8 : ntiles;
+    const uint32_t cap = (uint32_t)c.level_cap;
     if (c.has_vals)
-      leaf_place_kernel<K, true><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                               c.leaf_tile_off, nitems, c.fused ? 1 : 0);
+      leaf_place_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                             c.leaf_tile_off, nitems, ntiles, cap, c.fused ? 1 : 0,
+                                                             c.hdr);
     else
-      leaf_place_kernel<K, false><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                                c.leaf_tile_off, nitems, c.fused ? 1 : 0);
+      leaf_place_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                              c.leaf_tile_off, nitems, ntiles, cap, c.fused ? 1 : 0,
+                                                              c.hdr);
     return cudaGetLastError();
   }
 
@@ -78,10 +96,12 @@ struct Launch {
     }
     const int src = (depth + 1) & 1, dst = depth & 1;
     const size_t off = (size_t)depth * c.level_cap;
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
+    const bool on_dev = ntiles == kCountOnDevice;
+    const uint32_t grid = on_dev ? (uint32_t)(sms * blocks_per_sm)
+                                 : (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
     level_pass_kernel<K, V, NS><<<grid, kPassThreads, bytes, c.stream>>>(
         (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.level_tile_off + off, nitems,
-        ntiles, c.hdr, c.lib_status);
+        ntiles, on_dev ? &c.hdr->level_ctr[depth] : nullptr, (uint32_t)c.level_cap, c.hdr, c.lib_status);
     return cudaGetLastError();
   }
 

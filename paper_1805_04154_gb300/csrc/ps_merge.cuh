@@ -148,11 +148,11 @@ __device__ __forceinline__ int32_t sub_corank(const typename E::Arr& X, int32_t 
 }
 
 template <class K, bool V>
-__global__ void __launch_bounds__(kSubThreads, 4)
-subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
-               const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
-               const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-               const int32_t* __restrict__ tasks, int fused, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+__device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+                                             const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
+                                             const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
+                                             const int32_t task, int fused, PlanHeader* __restrict__ hdr,
+                                             uint32_t* lib_status) {
   typedef typename K::T T;
   typedef SubElem<K> E;
   typedef typename E::R R;
@@ -169,7 +169,6 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
   __shared__ int32_t s_maxrd;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int32_t task = tasks[blockIdx.x];
   int32_t L, R_, droot;
   if (task >= 0) {
     L = nodeL[task];
@@ -406,6 +405,24 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
   }
 }
 
+// One CTA per task, or (ntasks == kCountOnDevice) a persistent grid over the plan's task count.
+template <class K, bool V>
+__global__ void __launch_bounds__(kSubThreads, 4)
+subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+               const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
+               const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
+               const int32_t* __restrict__ tasks, uint32_t ntasks, uint32_t cap, int fused,
+               PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+  if (ntasks == kCountOnDevice) {
+    if (hdr->status & kDevBadOffsets) return;  // nothing moves when the offsets were rejected
+    ntasks = min(hdr->n_small, cap);
+  }
+  for (uint32_t tb = blockIdx.x; tb < ntasks; tb += gridDim.x) {
+    subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[tb], fused, hdr, lib_status);
+    __syncthreads();  // the next task reuses the shared arrays
+  }
+}
+
 // tile t -> item slot: largest s with tile_off[s] <= t
 __device__ __forceinline__ int32_t slot_of_tile(const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t t) {
   int32_t a = 0, b = (int32_t)nitems;
@@ -422,18 +439,18 @@ __device__ __forceinline__ int32_t slot_of_tile(const uint32_t* __restrict__ til
 // (or pairs).
 // ---------------------------------------------------------------------------------------
 template <class K, bool V>
-__global__ void __launch_bounds__(256)
-leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
-                  const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                  const uint32_t* __restrict__ tile_off, uint32_t nitems, int fused) {
+__device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+                                                const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
+                                                const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t tile,
+                                                int fused) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
   __shared__ int32_t s_slot;
-  if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, blockIdx.x);
+  if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, tile);
   __syncthreads();
   const int32_t slot = s_slot;
   const int32_t i = items[slot];
-  const int32_t k = (int32_t)(blockIdx.x - tile_off[slot]);
+  const int32_t k = (int32_t)(tile - tile_off[slot]);
   const int32_t s = S[i], e = S[i + 1];
   const bool desc = run_desc[i] != 0;
   const T* __restrict__ k0 = (const T*)buf.k[0];
@@ -493,6 +510,26 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
         }
       }
     }
+  }
+}
+
+// One CTA per tile, or (ntiles == kCountOnDevice) a persistent grid over the plan's counts.
+template <class K, bool V>
+__global__ void __launch_bounds__(256)
+leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+                  const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
+                  const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t ntiles, uint32_t cap, int fused,
+                  const PlanHeader* __restrict__ hdr) {
+  if (ntiles == kCountOnDevice) {
+    if (hdr->status & kDevBadOffsets) return;
+    const unsigned long long v = hdr->leaf_ctr;
+    nitems = min((uint32_t)(v >> 32), cap);
+    ntiles = (uint32_t)(v & 0xffffffffull);
+    if (nitems == 0) return;
+  }
+  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    leaf_place_tile<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, tile, fused);
+    __syncthreads();  // s_slot is rewritten by the next tile
   }
 }
 
@@ -596,9 +633,17 @@ __global__ void __launch_bounds__(kPassThreads, 4)
 level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __restrict__ srcv,
                   typename K::T* __restrict__ dstk, uint32_t* __restrict__ dstv,
                   const int4* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
-                  uint32_t ntiles, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+                  uint32_t ntiles, const unsigned long long* __restrict__ ctr, uint32_t cap,
+                  PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
   typedef typename K::T T;
   typedef PassLayout<K, V, NS> Lay;
+  if (ctr != nullptr) {  // counts from the plan on the device (no host round trip)
+    if (hdr->status & kDevBadOffsets) return;
+    const unsigned long long v = *ctr;
+    nitems = (uint32_t)(v >> 32);
+    ntiles = (uint32_t)(v & 0xffffffffull);
+    if (nitems > cap) return;  // the plan posted an internal error already
+  }
   constexpr int KU = Lay::KU;
   constexpr int kPassStages = NS;
   extern __shared__ __align__(128) uint8_t smem[];
@@ -610,6 +655,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
   const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  if (t_begin >= t_end) return;  // no tile for this CTA (uniform over the CTA)
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPassStages; ++s) {
       mbar_init(&full[s], 1);

@@ -635,6 +635,20 @@ cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped) {
   return cudaGetLastError();
 }
 
+// Device-driven calls: status bits the plan posted in the header reach the library's status
+// word (read by ps_stream_status) without a host round trip.
+__global__ void status_out_kernel(const PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+  if (threadIdx.x == 0 && lib_status != nullptr) {
+    const uint32_t st = hdr->status;
+    if (st) atomicOr(lib_status, st);
+  }
+}
+
+cudaError_t launch_status_out(const Ctx& c) {
+  status_out_kernel<<<1, 32, 0, c.stream>>>(c.hdr, c.lib_status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_check_offsets(const Ctx& c) {
   check_offsets_kernel<<<persistent_blocks(1), 256, 0, c.stream>>>(c.offsets, c.count, c.n, c.hdr);
   return cudaGetLastError();

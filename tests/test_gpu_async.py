@@ -1,0 +1,128 @@
+"""GPU parity of the device-driven entry point (ps_sort_async_ws: no host round trip, every
+launch sized from the plan on the device) against the CPU oracle, its device-side error path,
+and CUDA-graph capture: one captured sort replayed on new inputs in the same buffers gives the
+oracle's result every time (one array and many segments)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import paper_1805_04154_gb300 as ps
+    from paper_1805_04154_gb300 import _build
+    _build.build()
+    ps.load()
+    return ps
+
+
+def _dev(a):
+    if a.dtype == np.uint32:
+        return torch.from_numpy(a.view(np.int32)).cuda()
+    if a.dtype == np.uint64:
+        return torch.from_numpy(a.view(np.int64)).cuda()
+    return torch.from_numpy(a).cuda()
+
+
+def _ws(ps, kt, n, seg=False, tree=0):
+    return torch.empty(ps.ps_workspace_size(kt, True, n, seg, tree), dtype=torch.uint8, device="cuda")
+
+
+@pytest.mark.parametrize("case", ["runs", "perm", "u64", "f32", "tiny", "peek"])
+def test_async_matches_oracle(ps, case):
+    tree, kt, ktn = 0, 0, "i32"
+    if case == "runs":
+        keys, vals = workloads.runs_i32(400001, seed=1, max_len=3000)
+    elif case == "perm":
+        keys, vals = workloads.perm_i32(1 << 18, seed=2)
+    elif case == "u64":
+        keys, vals = workloads.pareto_u64(1 << 19, seed=3)
+        kt, ktn = 2, "u64"
+    elif case == "f32":
+        keys, vals = workloads.pareto_f32(1 << 18, seed=4)
+        kt, ktn = 3, "f32"
+    elif case == "tiny":
+        keys, vals = workloads.runs_i32(5, seed=5, max_len=3)
+    else:
+        keys, vals = workloads.runs_i32(300001, seed=6, max_len=900)
+        tree = 1
+    ref = oracle.powersort(keys, vals, kt=ktn)
+    dk, dv = _dev(keys), _dev(vals)
+    ps.ps_sort_async_ws(dk, dv, _ws(ps, kt, keys.size, False, tree), tree=tree, key_type=kt)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy().view(keys.dtype), ref.keys)
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+
+
+def test_async_segmented_and_bad_offsets(ps):
+    keys, vals, off = workloads.segmented_i32(300, seed=7, lo_exp=0, hi_exp=15)
+    ref = oracle.sort_segmented(keys, vals, off)
+    dk, dv, doff = _dev(keys), _dev(vals), torch.from_numpy(off).cuda()
+    ps.ps_sort_async_ws(dk, dv, _ws(ps, 0, keys.size, True), offsets=doff, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
+    # offsets that decrease: found on the device, reported by ps_stream_status, nothing moves
+    k2, v2 = workloads.runs_i32(1000, seed=8)
+    dk, dv = _dev(k2), _dev(v2)
+    before = dk.clone()
+    bad = torch.tensor([0, 600, 400, 1000], dtype=torch.int64, device="cuda")
+    ps.ps_sort_async_ws(dk, dv, _ws(ps, 0, 1000, True), offsets=bad, key_type=0)
+    assert ps.ps_stream_status() == 1
+    assert torch.equal(dk, before)
+    assert ps.ps_stream_status() == 0  # the status word was read and cleared
+
+
+def test_cuda_graph_capture_and_replay(ps):
+    n = 250003
+    dk = torch.empty(n, dtype=torch.int32, device="cuda")
+    dv = torch.empty(n, dtype=torch.int32, device="cuda")
+    ws = _ws(ps, 0, n)
+    keys0, vals0 = workloads.runs_i32(n, seed=10, max_len=1000)
+    dk.copy_(_dev(keys0))
+    dv.copy_(_dev(vals0))
+    ps.ps_sort_async_ws(dk, dv, ws, key_type=0)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ps.ps_sort_async_ws(dk, dv, ws, key_type=0)
+    for seed in (11, 12, 13):
+        keys, vals = workloads.runs_i32(n, seed=seed, max_len=int(2 * np.sqrt(n)))
+        dk.copy_(_dev(keys))
+        dv.copy_(_dev(vals))
+        g.replay()
+        torch.cuda.synchronize()
+        assert ps.ps_stream_status() == 0
+        ref = oracle.powersort(keys, vals)
+        np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
+        np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+
+
+def test_cuda_graph_segmented_replay(ps):
+    keys, vals, off = workloads.segmented_i32(500, seed=14, lo_exp=4, hi_exp=14)
+    n = keys.size
+    dk, dv, doff = _dev(keys), _dev(vals), torch.from_numpy(off).cuda()
+    ws = _ws(ps, 0, n, True)
+    ps.ps_sort_async_ws(dk, dv, ws, offsets=doff, key_type=0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ps.ps_sort_async_ws(dk, dv, ws, offsets=doff, key_type=0)
+    rng = np.random.default_rng(15)
+    for _ in range(2):
+        # new keys with the same segment layout
+        k2 = rng.integers(-1000, 1000, size=n, dtype=np.int32)
+        v2 = np.arange(n, dtype=np.uint32)
+        dk.copy_(_dev(k2))
+        dv.copy_(_dev(v2))
+        g.replay()
+        torch.cuda.synchronize()
+        assert ps.ps_stream_status() == 0
+        ref = oracle.sort_segmented(k2, v2, off)
+        np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
+        np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
