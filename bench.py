@@ -191,6 +191,29 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
             best = ms if best is None else min(best, ms)
     batched_ms = best
     out_k, out_v = dk.clone(), dv.clone()
+    # the same batch as one captured CUDA graph of the device-driven entry, replayed
+    gk, gv = k0.clone(), v0.clone()
+    wsg = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n, True), dtype=torch.uint8, device=dev)
+    ps.ps_sort_async_ws(gk, gv, wsg, offsets=doff, key_type=ps.PS_KEY_I32, stream=stream)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ps.ps_sort_async_ws(gk, gv, wsg, offsets=doff, key_type=ps.PS_KEY_I32)
+    gbest = None
+    for rep in range(reps + 1):
+        gk.copy_(k0)
+        gv.copy_(v0)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if rep > 0:
+            ms = e0.elapsed_time(e1)
+            gbest = ms if gbest is None else min(gbest, ms)
+    graph_identical = bool(torch.equal(out_k, gk)) and bool(torch.equal(out_v, gv)) and ps.ps_stream_status() == 0
+    del graph, gk, gv, wsg
     # one plain ps_sort_ws per array on the same data (workspace sized for the largest array)
     dk.copy_(k0)
     dv.copy_(v0)
@@ -213,7 +236,9 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
             "batched_ms": batched_ms, "batched_gkeys_s": n / (batched_ms / 1e3) / 1e9,
             "plain_loop_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
             "speedup": plain_ms / batched_ms, "identical_results": identical,
+            "graph_ms": gbest, "graph_gkeys_s": n / (gbest / 1e3) / 1e9, "graph_identical_results": graph_identical,
             "batched_entry": "ps_sort_segmented_ws (one call)",
+            "graph_entry": "ps_sort_async_ws captured once in a CUDA graph, replayed",
             "plain_entry": "ps_sort_ws per array"}
 
 
@@ -355,6 +380,9 @@ def run_gpu(args):
     dk0 = torch.from_numpy(keys).to(dev)
     dv0 = torch.from_numpy(vals.view(np.int32)).to(dev)
     an = ps.ps_analyze(dk0, key_type=ps.PS_KEY_I32)
+    # the library's autotuner picks the level-pass configuration on this input (outside the
+    # timed region; the input is left unchanged)
+    tune = None if args.no_tune else ps.ps_autotune(dk0, dv0, key_type=ps.PS_KEY_I32)
     M = an["cost"]
     lengths = np.diff(an["starts"]).astype(np.float64)
     H = float(-(lengths / n * np.log2(lengths / n)).sum())
@@ -471,6 +499,9 @@ def run_gpu(args):
             "plan": {"runs": int(an["runs"]), "merge_cost": int(M), "entropy_bits": H,
                      "max_leaf_depth": int(an["leaf_depth"].max())},
             "stages_ms_per_step": stages_ms, "gpu_launches": int(launches), "clocks": clocks,
+            "level_pass_config": {"items_per_thread": ps.ps_tune_get(ps.PS_KEY_I32, True)[0],
+                                  "stages": ps.ps_tune_get(ps.PS_KEY_I32, True)[1],
+                                  "autotune": tune},
             "sorted_check": ok}
 
     # end to end through the C ABI with host buffers (pinned), every step H2D + sort + D2H:
@@ -591,6 +622,7 @@ def main():
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--n", type=int, default=N_DEFAULT, help="array size (default 1e8)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default level-pass configuration")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the 10,000-array batched measurement")
     ap.add_argument("--no-variants", action="store_true", help="skip the other single-array workloads")

@@ -150,6 +150,33 @@ size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segment
 ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
                           int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Level-pass configuration and its autotuner.  A level pass splits its merges into tiles of
+ * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
+ * shared-memory buffers; the library carries the configurations (12, 2), (12, 3), (12, 4),
+ * (8, 2), (8, 3) and (16, 2).  One configuration per key type and payload choice is used by every
+ * later sort on this process (default (12, 2)). */
+typedef struct {
+  int items_per_thread;    /* the chosen configuration */
+  int stages;
+  int n_variants;          /* configurations timed below */
+  int variant_items[8];
+  int variant_stages[8];
+  double variant_ms[8];    /* median device time of one whole sort of the given array */
+} ps_tune_result;
+
+/* Time every configuration on copies of the caller's device array keys[0..n) (vals may be NULL;
+ * neither is modified; scratch from the library's pool), keep the fastest for this key type and
+ * payload choice, and report all timings.  Synchronizes the stream. */
+ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, ps_tune_result* out,
+                      void* stream);
+
+/* Set the configuration for a key type and payload choice (0, 0: back to the default);
+ * PS_ERR_UNSUPPORTED for a configuration the library does not carry. */
+ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages);
+
+/* The configuration in use for a key type and payload choice. */
+ps_status ps_tune_get(int key_type, int has_vals, int* items_per_thread, int* stages);
+
 /* Device-driven sort: as ps_sort_tree_ws (d_offsets NULL, count 1 for one array), but with no
  * host round trip -- every launch after planning takes its work count from the plan on the
  * device (persistent grids; one level-pass launch per depth the tree can have, empty ones return

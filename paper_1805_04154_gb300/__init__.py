@@ -22,7 +22,7 @@ __all__ = [
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
     "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
-    "ps_sort_tree", "ps_sort_host_ws", "ps_sort_async_ws",
+    "ps_sort_tree", "ps_sort_host_ws", "ps_sort_async_ws", "ps_autotune", "ps_tune_set", "ps_tune_get",
 ]
 
 STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
@@ -88,6 +88,9 @@ def load():
                 "ps_workspace_size_tree": ([i32, i32, i64, i32, i32], sz),
                 "ps_sort_host_ws": ([i32, vp, vp, vp, vp, i64, vp, vp, vp, sz, vp], i32),
                 "ps_sort_async_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+                "ps_autotune": ([i32, vp, vp, i64, vp, vp], i32),
+                "ps_tune_set": ([i32, i32, i32, i32], i32),
+                "ps_tune_get": ([i32, i32, vp, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
@@ -348,3 +351,32 @@ def ps_sort_async_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: t
                                    _dev_ptr(offsets, "offsets") if seg else None,
                                    (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(workspace, "workspace"),
                                    workspace.numel(), _stream_ptr(stream, keys.device)), "ps_sort_async_ws")
+
+
+class _Tune(ctypes.Structure):
+    _fields_ = [("items_per_thread", ctypes.c_int), ("stages", ctypes.c_int), ("n_variants", ctypes.c_int),
+                ("variant_items", ctypes.c_int * 8), ("variant_stages", ctypes.c_int * 8),
+                ("variant_ms", ctypes.c_double * 8)]
+
+
+def ps_autotune(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: int | None = None,
+                stream=None) -> dict:
+    """Time every level-pass configuration on copies of ``keys``/``vals`` (unchanged) and keep the
+    fastest for this key type and payload choice; returns the choice and all timings."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    out = _Tune()
+    _check(load().ps_autotune(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(), ctypes.byref(out),
+                              _stream_ptr(stream, keys.device)), "ps_autotune")
+    return {"items_per_thread": out.items_per_thread, "stages": out.stages,
+            "variants": [{"items_per_thread": out.variant_items[i], "stages": out.variant_stages[i],
+                          "ms": out.variant_ms[i]} for i in range(out.n_variants)]}
+
+
+def ps_tune_set(key_type: int, has_vals: bool, items_per_thread: int, stages: int) -> None:
+    _check(load().ps_tune_set(key_type, 1 if has_vals else 0, items_per_thread, stages), "ps_tune_set")
+
+
+def ps_tune_get(key_type: int, has_vals: bool) -> tuple[int, int]:
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().ps_tune_get(key_type, 1 if has_vals else 0, ctypes.byref(a), ctypes.byref(b)), "ps_tune_get")
+    return a.value, b.value

@@ -182,15 +182,35 @@ struct AnalyzeOut {
   ps_stats* stats;
 };
 
-// Level-pass ring depth: PS_PASS_STAGES (2, 3, 4 or 6) overrides the default for tuning runs.
-int pass_stages_setting() {
+// Level-pass configuration (items per consumer thread, ring stages), per key type and payload
+// choice: 12 items and 2 stages unless PS_PASS_STAGES picks another compiled ring depth for 12
+// items, ps_tune_set or ps_autotune choose otherwise.  Packed as pass_variant(ipt, stages).
+bool known_variant(int ipt, int stages) {
+  for (int i = 0; i < kPassVariants; ++i)
+    if (kPassVariantIpt[i] == ipt && kPassVariantStages[i] == stages) return true;
+  return false;
+}
+
+int default_variant() {
   static int v = -1;
   if (v < 0) {
     const char* e = std::getenv("PS_PASS_STAGES");
-    int x = e ? std::atoi(e) : 0;
-    v = (x == 2 || x == 3 || x == 4 || x == 6) ? x : 2;
+    const int x = e ? std::atoi(e) : 0;
+    v = known_variant(kMergeItems, x) ? pass_variant(kMergeItems, x) : pass_variant(kMergeItems, 2);
   }
   return v;
+}
+
+std::atomic<int> g_tune[4][2];  // 0 = default
+thread_local int t_variant_override = 0;  // set by the autotuner around its trial sorts
+
+void apply_pass_config(Ctx& c, int kt, bool vals) {
+  int v = t_variant_override;
+  if (!v) v = g_tune[kt][vals ? 1 : 0].load();
+  if (!v) v = default_variant();
+  c.pass_ipt = v / 16;
+  c.pass_stages = v % 16;
+  c.merge_tile = c.pass_ipt * kMergeThreads;
 }
 
 // Binary passes (one tree level per HBM pass) unless PS_FUSED=1 selects fused passes (two tree
@@ -291,7 +311,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
-  c.pass_stages = pass_stages_setting();
+  apply_pass_config(c, kt, vals != nullptr);
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
@@ -321,6 +341,9 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
   const int32_t r = h.runs;
   if (r < 1 || r > n) return PS_ERR_INTERNAL;
+  // the counts the merge launches are sized with must fit the plan's arrays
+  if ((uint64_t)h.n_small > (uint64_t)n + 2) return PS_ERR_INTERNAL;
+  if ((h.leaf_ctr >> 32) > (uint64_t)c.level_cap || (h.leaf_ctr & 0xffffffffull) > (uint64_t)n) return PS_ERR_INTERNAL;
 
   if (an) {
     if (an->runs) *an->runs = r;
@@ -368,6 +391,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
     if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
+    if (!c.fused && (uint64_t)tiles > (uint64_t)n / (uint64_t)c.merge_tile + 2ull * items + 1) return PS_ERR_INTERNAL;
     if (c.fused) {
       // fused passes exist at even depths only; tiles counts chunk-boundary slots
       if ((d & 1) || (uint64_t)tiles > chunk_capacity(n, (size_t)c.level_cap)) return PS_ERR_INTERNAL;
@@ -411,7 +435,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
   if (!c.lib_status) return PS_ERR_CUDA;
-  c.pass_stages = pass_stages_setting();
+  apply_pass_config(c, kt, vals != nullptr);
   const KeyLaunch* kl = launch_for(kt);
   // deepest node: depth < power <= floor(lg n) + 1 for Alg. 2; the plan's limit for Alg. 1
   int maxd = kMaxLevels - 1;
@@ -585,6 +609,98 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
   const bool seg = d_offsets != nullptr;
   return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
              workspace_bytes, (cudaStream_t)stream, &an);
+}
+
+ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages) {
+  if (!launch_for(key_type)) return PS_ERR_INVALID_ARG;
+  if (items_per_thread == 0 && stages == 0) {  // back to the default
+    g_tune[key_type][has_vals ? 1 : 0].store(0);
+    return PS_OK;
+  }
+  if (!known_variant(items_per_thread, stages)) return PS_ERR_UNSUPPORTED;
+  g_tune[key_type][has_vals ? 1 : 0].store(pass_variant(items_per_thread, stages));
+  return PS_OK;
+}
+
+ps_status ps_tune_get(int key_type, int has_vals, int* items_per_thread, int* stages) {
+  if (!launch_for(key_type) || !items_per_thread || !stages) return PS_ERR_INVALID_ARG;
+  Ctx c;
+  apply_pass_config(c, key_type, has_vals != 0);
+  *items_per_thread = c.pass_ipt;
+  *stages = c.pass_stages;
+  return PS_OK;
+}
+
+ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, ps_tune_result* out,
+                      void* stream) {
+  ps_status st = check_args(key_type, keys, vals, n);
+  if (st != PS_OK) return st;
+  if (!out || n < 2) return PS_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  cudaMemPool_t pool = lib_pool(dev);
+  if (!pool) return PS_ERR_CUDA;
+  const size_t kb = (size_t)key_bytes(key_type);
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals ? up((size_t)n * 4 + 16) : 0;
+  Ctx tmp;
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals != nullptr, n, false, fused_setting());
+  uint8_t* base = nullptr;
+  if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
+    return PS_ERR_OUT_OF_MEMORY;
+  void* dk = base;
+  uint32_t* dv = vals ? (uint32_t*)(base + kbytes) : nullptr;
+  void* ws = base + kbytes + vbytes;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::memset(out, 0, sizeof(*out));
+  int best = -1;
+  double best_ms = 0.0;
+  constexpr int kReps = 3;
+  for (int i = 0; i < kPassVariants && st == PS_OK; ++i) {
+    t_variant_override = pass_variant(kPassVariantIpt[i], kPassVariantStages[i]);
+    double t[kReps];
+    for (int rep = 0; rep <= kReps && st == PS_OK; ++rep) {  // rep 0 warms up
+      cudaError_t e = cudaMemcpyAsync(dk, keys, (size_t)n * kb, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess && dv) e = cudaMemcpyAsync(dv, vals, (size_t)n * 4, cudaMemcpyDeviceToDevice, s);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+      if (e != cudaSuccess) {
+        st = cuda_status(e);
+        break;
+      }
+      st = run(key_type, dk, dv, n, nullptr, 1, false, ws, wbytes, s, nullptr);
+      if (st != PS_OK) break;
+      e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      float ms = 0.f;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess) st = cuda_status(e);
+      if (rep > 0) t[rep - 1] = ms;
+    }
+    if (st != PS_OK) break;
+    std::sort(t, t + kReps);
+    const double med = t[kReps / 2];
+    out->variant_items[i] = kPassVariantIpt[i];
+    out->variant_stages[i] = kPassVariantStages[i];
+    out->variant_ms[i] = med;
+    out->n_variants = i + 1;
+    if (best < 0 || med < best_ms) {
+      best = i;
+      best_ms = med;
+    }
+  }
+  t_variant_override = 0;
+  cudaFreeAsync(base, s);
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != PS_OK) return st;
+  g_tune[key_type][vals ? 1 : 0].store(pass_variant(kPassVariantIpt[best], kPassVariantStages[best]));
+  out->items_per_thread = kPassVariantIpt[best];
+  out->stages = kPassVariantStages[best];
+  return PS_OK;
 }
 
 ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,

@@ -24,6 +24,13 @@ constexpr int kTreeThreads = 256;
 constexpr int kTreeChunk = 32;
 constexpr int kTreeTile = kTreeThreads * kTreeChunk;  // 8192
 
+// Level-pass configurations (items per consumer thread, shared-memory ring stages) compiled
+// into the library; the tile of a pass is items x kMergeThreads outputs.
+__host__ __device__ constexpr int pass_variant(int ipt, int stages) { return ipt * 16 + stages; }
+constexpr int kPassVariants = 6;
+constexpr int kPassVariantIpt[kPassVariants] = {12, 12, 12, 8, 8, 16};
+constexpr int kPassVariantStages[kPassVariants] = {2, 3, 4, 2, 3, 2};
+
 // Stage 4 (merge passes over HBM): one CTA produces kMergeTile outputs of one merge.
 constexpr int kMergeThreads = 256;
 constexpr int kMergeItems = 12;

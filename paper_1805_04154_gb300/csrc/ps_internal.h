@@ -42,7 +42,9 @@ struct Ctx {
   int32_t* tree_pre = nullptr;
 
   int32_t sub_lim = 0;          // subtree-in-SMEM element limit
-  int pass_stages = 2;          // shared-memory stages of the level-pass ring (2, 3, 4 or 6)
+  int pass_stages = 2;          // shared-memory stages of the level-pass ring
+  int pass_ipt = kMergeItems;   // outputs per consumer thread of a level pass
+  int32_t merge_tile = kMergeTile;  // outputs per level-pass tile (pass_ipt x kMergeThreads)
   bool fused = false;           // fused passes (two tree levels per HBM pass) or binary passes
   int tree = 0;                 // merge tree: 0 powersort (Alg. 2), 1 peeksort (Alg. 1)
   int2* peek_front[2] = {nullptr, nullptr};  // peeksort: run ranges of one tree level

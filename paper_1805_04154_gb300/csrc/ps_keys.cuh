@@ -77,20 +77,20 @@ struct Launch {
     return cudaGetLastError();
   }
 
-  template <bool V, int NS>
+  template <bool V, int NS, int IPT>
   static cudaError_t merge_vs(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
     static int blocks_per_sm = 0;
     static int sms = 0;
-    const size_t bytes = PassLayout<K, V, NS>::kBytes;
+    const size_t bytes = PassLayout<K, V, NS, IPT>::kBytes;
     if (blocks_per_sm == 0) {
-      cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<K, V, NS>,
+      cudaError_t e = cudaFuncSetAttribute(level_pass_kernel<K, V, NS, IPT>,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
       if (e != cudaSuccess) return e;
       int dev = 0;
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, level_pass_kernel<K, V, NS>, kPassThreads,
-                                                        bytes);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, level_pass_kernel<K, V, NS, IPT>,
+                                                        kPassThreads, bytes);
       if (e != cudaSuccess) return e;
       if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -99,19 +99,23 @@ struct Launch {
     const bool on_dev = ntiles == kCountOnDevice;
     const uint32_t grid = on_dev ? (uint32_t)(sms * blocks_per_sm)
                                  : (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
-    level_pass_kernel<K, V, NS><<<grid, kPassThreads, bytes, c.stream>>>(
+    level_pass_kernel<K, V, NS, IPT><<<grid, kPassThreads, bytes, c.stream>>>(
         (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.level_tile_off + off, nitems,
         ntiles, on_dev ? &c.hdr->level_ctr[depth] : nullptr, (uint32_t)c.level_cap, c.hdr, c.lib_status);
     return cudaGetLastError();
   }
 
+  // the level-pass configurations the library carries (items per thread, ring stages); the
+  // autotuner chooses among them
   template <bool V>
   static cudaError_t merge_v(const Ctx& c, int depth, uint32_t nitems, uint32_t ntiles) {
-    switch (c.pass_stages) {
-      case 3: return merge_vs<V, 3>(c, depth, nitems, ntiles);
-      case 4: return merge_vs<V, 4>(c, depth, nitems, ntiles);
-      case 6: return merge_vs<V, 6>(c, depth, nitems, ntiles);
-      default: return merge_vs<V, 2>(c, depth, nitems, ntiles);
+    switch (pass_variant(c.pass_ipt, c.pass_stages)) {
+      case pass_variant(12, 3): return merge_vs<V, 3, 12>(c, depth, nitems, ntiles);
+      case pass_variant(12, 4): return merge_vs<V, 4, 12>(c, depth, nitems, ntiles);
+      case pass_variant(8, 2): return merge_vs<V, 2, 8>(c, depth, nitems, ntiles);
+      case pass_variant(8, 3): return merge_vs<V, 3, 8>(c, depth, nitems, ntiles);
+      case pass_variant(16, 2): return merge_vs<V, 2, 16>(c, depth, nitems, ntiles);
+      default: return merge_vs<V, 2, 12>(c, depth, nitems, ntiles);
     }
   }
 

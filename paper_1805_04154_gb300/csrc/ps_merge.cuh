@@ -14,7 +14,7 @@
 //                        reversed.
 //  * level_pass_kernel   persistent, warp-specialized level pass: a producer warp finds each
 //                        tile's co-rank and stages both input ranges into shared memory with bulk
-//                        (TMA) copies on mbarriers; consumer warps merge kMergeItems outputs per
+//                        (TMA) copies on mbarriers; consumer warps merge IPT outputs per
 //                        thread and write them with 128-bit stores.
 #pragma once
 
@@ -169,6 +169,11 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
   __shared__ int32_t s_maxrd;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int32_t runs = hdr->runs;
+  if (task >= runs || (task < 0 && ~task >= runs)) {  // never for a consistent plan
+    if (tid == 0) post_status(&hdr->status, lib_status, kDevInternal);
+    return;
+  }
   int32_t L, R_, droot;
   if (task >= 0) {
     L = nodeL[task];
@@ -178,6 +183,10 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
     L = ~task;
     R_ = L + 1;
     droot = ldepth[L];
+  }
+  if (L < 0 || R_ > runs || L >= R_) {
+    if (tid == 0) post_status(&hdr->status, lib_status, kDevInternal);
+    return;
   }
   const int32_t lo = S[L], m = S[R_] - lo, nr = R_ - L;
   if (m > TS || nr + 1 > RC) {  // cannot happen for a greedy run partition; never overrun SMEM
@@ -442,7 +451,7 @@ template <class K, bool V>
 __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                                                 const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                                                 const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t tile,
-                                                int fused) {
+                                                int fused, int32_t runs) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
   __shared__ int32_t s_slot;
@@ -450,6 +459,7 @@ __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restr
   __syncthreads();
   const int32_t slot = s_slot;
   const int32_t i = items[slot];
+  if (i < 0 || i >= runs) return;  // never for a consistent plan (uniform over the CTA)
   const int32_t k = (int32_t)(tile - tile_off[slot]);
   const int32_t s = S[i], e = S[i + 1];
   const bool desc = run_desc[i] != 0;
@@ -527,24 +537,25 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
     ntiles = (uint32_t)(v & 0xffffffffull);
     if (nitems == 0) return;
   }
+  const int32_t runs = hdr->runs;
   for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    leaf_place_tile<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, tile, fused);
+    leaf_place_tile<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, tile, fused, runs);
     __syncthreads();  // s_slot is rewritten by the next tile
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // One level pass: all merges of the tree nodes at one depth whose ranges exceed the subtree
-// limit, split into output tiles that start at the node's lo and then at the multiples of
-// kMergeTile inside it.  Persistent and warp-specialized:
+// limit, split into output tiles that start at the node's lo and then at the multiples of the
+// tile size (IPT outputs per consumer thread x 256 threads) inside it.  Persistent and warp-specialized:
 //  * CTA b owns the contiguous tile range [b*T/G, (b+1)*T/G) of the pass (T tiles, G CTAs), so
 //    the co-rank at the end of one tile is the co-rank at the start of the next;
 //  * warp 8 (producer) walks the CTA's tiles: it finds each tile's end co-rank with a 32-way
-//    warp search inside the window the start co-rank allows (at most kMergeTile wide; its
+//    warp search inside the window the start co-rank allows (at most one tile wide; its
 //    probes touch the lines the tile's copy then reads), waits for a free stage, and issues the
 //    tile's four bulk copies (left/right keys and payloads, 16-byte aligned chunks) on that
 //    stage's "full" mbarrier;
-//  * warps 0-7 (consumers) wait for a full stage, merge its kMergeItems outputs per thread
+//  * warps 0-7 (consumers) wait for a full stage, merge its IPT outputs per thread
 //    (co-rank inside shared memory, then a serial stable merge), write them with 128-bit
 //    stores, and release the stage on its "empty" mbarrier.
 // A ring of NS stages: the copies of the next NS-1 tiles overlap the merge of the current one.
@@ -559,13 +570,14 @@ struct StageDesc {
   int32_t pad[4];
 };
 
-template <class K, bool V, int NS>
+template <class K, bool V, int NS, int IPT>
 struct PassLayout {
   typedef typename K::T T;
   static constexpr int kStages = NS;
+  static constexpr int kTile = IPT * kMergeThreads;
   static constexpr int KU = 16 / (int)sizeof(T);
-  static constexpr int KCAP = kMergeTile + 4 * KU;
-  static constexpr int VCAP = kMergeTile + 16;
+  static constexpr int KCAP = kTile + 4 * KU;
+  static constexpr int VCAP = kTile + 16;
   static constexpr size_t kKeyBytes = ((size_t)KCAP * sizeof(T) + 127) & ~(size_t)127;
   static constexpr size_t kValBytes = V ? (((size_t)VCAP * 4 + 127) & ~(size_t)127) : 0;
   static constexpr size_t kStageBytes = kKeyBytes + kValBytes;
@@ -628,15 +640,19 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
   return true;
 }
 
-template <class K, bool V, int NS>
-__global__ void __launch_bounds__(kPassThreads, 4)
+// CTAs per SM the register budget is sized for (16 items per thread need more registers).
+__host__ __device__ constexpr int pass_min_blocks(int ipt) { return ipt <= 12 ? 4 : 3; }
+
+template <class K, bool V, int NS, int IPT>
+__global__ void __launch_bounds__(kPassThreads, pass_min_blocks(IPT))
 level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __restrict__ srcv,
                   typename K::T* __restrict__ dstk, uint32_t* __restrict__ dstv,
                   const int4* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
                   uint32_t ntiles, const unsigned long long* __restrict__ ctr, uint32_t cap,
                   PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
   typedef typename K::T T;
-  typedef PassLayout<K, V, NS> Lay;
+  typedef PassLayout<K, V, NS, IPT> Lay;
+  constexpr int kTile = Lay::kTile;
   if (ctr != nullptr) {  // counts from the plan on the device (no host round trip)
     if (hdr->status & kDevBadOffsets) return;
     const unsigned long long v = *ctr;
@@ -676,7 +692,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     const T* A = srck + nd.x;
     const T* B = srck + nd.y;
     const int32_t k0 = (int32_t)(t_begin - tile_off[slot]);
-    int32_t g0 = (k0 == 0) ? nd.x : (nd.x / kMergeTile + k0) * kMergeTile;
+    int32_t g0 = (k0 == 0) ? nd.x : (nd.x / kTile + k0) * kTile;
     int32_t i0 = 0;
     if (g0 > nd.x) {
       const int32_t diag = g0 - nd.x;
@@ -713,7 +729,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
               ai = 0;
               m_new[m] = true;
             }
-            const int32_t g1 = min(cnd.z, (cg0 / kMergeTile + 1) * kMergeTile);
+            const int32_t g1 = min(cnd.z, (cg0 / kTile + 1) * kTile);
             const int32_t cla = cnd.y - cnd.x, clb = cnd.z - cnd.y, diag = g1 - cnd.x;
             m_nd[m] = cnd;
             m_slot[m] = cs;
@@ -875,18 +891,18 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       const T* B = (const T*)stage + d.boff;
       const uint32_t* sv = (const uint32_t*)(stage + Lay::kKeyBytes);
       const int32_t len = d.g1 - d.g0, la = d.i1 - d.i0, lb = len - la;
-      const int32_t diag = tid * kMergeItems;
+      const int32_t diag = tid * IPT;
       if (diag < len) {
         int32_t i = corank_serial<K>(A, B, la, lb, diag);
         int32_t j = diag - i;
-        const int32_t cnt = min(kMergeItems, len - diag);
-        T key[kMergeItems];
-        uint32_t val[kMergeItems];
+        const int32_t cnt = min(IPT, len - diag);
+        T key[IPT];
+        uint32_t val[IPT];
         // heads of both inputs stay in registers: one shared-memory key read per output
         T a = A[min(i, la - 1 >= 0 ? la - 1 : 0)], b = B[min(j, lb - 1 >= 0 ? lb - 1 : 0)];
-        if (cnt == kMergeItems) {
+        if (cnt == IPT) {
 #pragma unroll
-          for (int q = 0; q < kMergeItems; ++q) {
+          for (int q = 0; q < IPT; ++q) {
             const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
             key[q] = takeA ? a : b;
             if (V) val[q] = sv[takeA ? d.vaoff + i : d.vboff + j];
@@ -900,7 +916,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < kMergeItems; ++q) {
+          for (int q = 0; q < IPT; ++q) {
             if (q < cnt) {
               const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
               key[q] = takeA ? a : b;
@@ -916,10 +932,10 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           }
         }
         const int32_t g = d.g0 + diag;
-        if (cnt == kMergeItems && ((uintptr_t)(dstk + g) & 15u) == 0) {
+        if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
           uint4* o = (uint4*)(dstk + g);
 #pragma unroll
-          for (int q = 0; q < kMergeItems / KU; ++q) {
+          for (int q = 0; q < IPT / KU; ++q) {
             uint4 w;
             T* wt = (T*)&w;
 #pragma unroll
@@ -928,18 +944,18 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           }
         } else {
 #pragma unroll
-          for (int q = 0; q < kMergeItems; ++q)
+          for (int q = 0; q < IPT; ++q)
             if (q < cnt) dstk[g + q] = key[q];
         }
         if (V) {
-          if (cnt == kMergeItems && ((uintptr_t)(dstv + g) & 15u) == 0) {
+          if (cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
             uint4* o = (uint4*)(dstv + g);
 #pragma unroll
-            for (int q = 0; q < kMergeItems / 4; ++q)
+            for (int q = 0; q < IPT / 4; ++q)
               o[q] = make_uint4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
           } else {
 #pragma unroll
-            for (int q = 0; q < kMergeItems; ++q)
+            for (int q = 0; q < IPT; ++q)
               if (q < cnt) dstv[g + q] = val[q];
           }
         }

@@ -90,7 +90,7 @@ __device__ __forceinline__ uint32_t load_power_window(const uint8_t* __restrict_
   const uint32_t* __restrict__ Pw = (const uint32_t*)P;
   const int32_t wa = b >> 2;  // floor(b / 4), also for negative b
   const uint32_t lo = (wa >= 0 && 4 * wa <= r) ? Pw[wa] : 0u;
-  const uint32_t hi = ((b & 3) != 0 && 4 * (wa + 1) <= r) ? Pw[wa + 1] : 0u;
+  const uint32_t hi = ((b & 3) != 0 && wa + 1 >= 0 && 4 * (wa + 1) <= r) ? Pw[wa + 1] : 0u;
   uint32_t w = __funnelshift_r(lo, hi, (uint32_t)(b & 3) * 8u);
   if (b < 0 || b + 3 > r) {
 #pragma unroll
@@ -414,7 +414,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
                             int4* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
                             int32_t level_cap, int32_t small_cap, int fused, int32_t* __restrict__ lsplit,
-                            int32_t* __restrict__ rsplit, PlanHeader* __restrict__ hdr) {
+                            int32_t* __restrict__ rsplit, int32_t merge_tile, PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   unsigned long long cost = 0;
   int32_t maxd = 0;
@@ -477,7 +477,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         const int d = ndepth[x];
         // binary passes: output tiles of kMergeTile; fused passes: chunk-boundary slots
         const uint32_t tiles = fused ? (uint32_t)(size / kChunkSpan + 2)
-                                     : (uint32_t)((hi - 1) / kMergeTile - lo / kMergeTile + 1);
+                                     : (uint32_t)((hi - 1) / merge_tile - lo / merge_tile + 1);
         if (d >= kMaxLevels) {
           post_status(&hdr->status, nullptr, kDevInternal);
         } else if (fused && (d & 1)) {
@@ -599,7 +599,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                             c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                             c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
-                                            c.lsplit, c.rsplit, c.hdr);
+                                            c.lsplit, c.rsplit, c.merge_tile, c.hdr);
     return cudaGetLastError();
   }
   node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
@@ -621,7 +621,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                           c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
-                                          c.lsplit, c.rsplit, c.hdr);
+                                          c.lsplit, c.rsplit, c.merge_tile, c.hdr);
   return cudaGetLastError();
 }
 

@@ -89,3 +89,15 @@ def test_tree_argument_errors_without_gpu(lib):
     assert lib.ps_sort_tree_ws(0, ctypes.c_void_p(4096), None, 10, None, 1, 7, ws, 1 << 20, None) == 1
     assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 7) == 0
     assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 1) > lib.ps_workspace_size_tree(0, 1, 1000, 0, 0)
+
+
+def test_tuning_table_without_gpu(lib):
+    import paper_1805_04154_gb300 as ps
+    assert ps.ps_tune_get(0, True) == (12, 2)
+    ps.ps_tune_set(0, True, 16, 2)
+    assert ps.ps_tune_get(0, True) == (16, 2)
+    assert ps.ps_tune_get(0, False) == (12, 2)
+    with pytest.raises(ps.PowersortError):
+        ps.ps_tune_set(0, True, 10, 2)  # not a configuration the library carries
+    ps.ps_tune_set(0, True, 0, 0)
+    assert ps.ps_tune_get(0, True) == (12, 2)
