@@ -472,8 +472,9 @@ def run_gpu(args):
             import hashlib
             with open(tpath) as f:
                 tr = json.load(f)
-            src = open(os.path.join(ROOT, "paper_1805_04154_gb300", "csrc", "ps_merge.cuh"), "rb").read()
-            if tr.get("source_sha256") == hashlib.sha256(src).hexdigest() and mt["launches"]:
+            csrc = os.path.join(ROOT, "paper_1805_04154_gb300", "csrc")
+            src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in tr.get("sources", []))
+            if src and tr.get("source_sha256") == hashlib.sha256(src).hexdigest() and mt["launches"]:
                 elems_per_launch = mt["bytes"] / (2 * eb) / mt["launches"]
                 traffic = tr["dram_bytes_per_output_elem"] * elems_per_launch
         except Exception:

@@ -23,6 +23,7 @@
 // All waits are bounded; a timeout posts kDevTimeout and the CTA drains its copies and exits.
 #pragma once
 
+#include "ps_level.cuh"
 #include "ps_merge.cuh"
 
 namespace ps {

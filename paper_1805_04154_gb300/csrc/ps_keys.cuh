@@ -7,6 +7,7 @@
 #include "ps_detect.cuh"
 #include "ps_internal.h"
 #include "ps_fused.cuh"
+#include "ps_level.cuh"
 #include "ps_merge.cuh"
 
 namespace ps {
@@ -45,15 +46,21 @@ struct Launch {
     if (!attr) {
       cudaError_t e = cudaFuncSetAttribute(subtree_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)bytes);
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(subtree_persistent_kernel<K, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)bytes);
       if (e != cudaSuccess) return e;
       attr = true;
     }
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
-    const uint32_t grid = ntasks == kCountOnDevice ? (uint32_t)sm_count() * 4 : ntasks;
-    subtree_kernel<K, V><<<grid, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth,
-                                                                  c.ldepth, c.small_tasks, ntasks,
-                                                                  (uint32_t)(c.n + 2), c.fused ? 1 : 0, c.hdr,
-                                                                  c.lib_status);
+    if (ntasks == kCountOnDevice)
+      subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 3, kSubThreads, bytes, c.stream>>>(
+          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)(c.n + 2),
+          c.fused ? 1 : 0, c.hdr, c.lib_status);
+    else
+      subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
+                                                                      c.ndepth, c.ldepth, c.small_tasks,
+                                                                      c.fused ? 1 : 0, c.hdr, c.lib_status);
     return cudaGetLastError();
   }
   static cudaError_t small(const Ctx& c, uint32_t ntasks) {
@@ -64,16 +71,24 @@ struct Launch {
   static cudaError_t place(const Ctx& c, uint32_t nitems, uint32_t ntiles) {
     if (ntiles == 0) return cudaSuccess;
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
-    const uint32_t grid = ntiles == kCountOnDevice ? (uint32_t)sm_count() * 8 : ntiles;
     const uint32_t cap = (uint32_t)c.level_cap;
-    if (c.has_vals)
-      leaf_place_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                             c.leaf_tile_off, nitems, ntiles, cap, c.fused ? 1 : 0,
-                                                             c.hdr);
-    else
-      leaf_place_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                              c.leaf_tile_off, nitems, ntiles, cap, c.fused ? 1 : 0,
-                                                              c.hdr);
+    const int fu = c.fused ? 1 : 0;
+    if (ntiles == kCountOnDevice) {
+      const uint32_t grid = (uint32_t)sm_count() * 8;
+      if (c.has_vals)
+        leaf_place_persistent_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                                          c.leaf_tile_off, cap, fu, c.hdr);
+      else
+        leaf_place_persistent_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth,
+                                                                           c.leaf_items, c.leaf_tile_off, cap, fu,
+                                                                           c.hdr);
+    } else if (c.has_vals) {
+      leaf_place_kernel<K, true><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                               c.leaf_tile_off, nitems, fu, c.hdr);
+    } else {
+      leaf_place_kernel<K, false><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                                c.leaf_tile_off, nitems, fu, c.hdr);
+    }
     return cudaGetLastError();
   }
 

@@ -1,0 +1,433 @@
+// Stage 4: the level pass -- all large merges of one tree depth in one persistent launch.
+// (Kept in its own file: the benchmark ties the level pass's recorded DRAM traffic to the hash of
+// this file and ps_common.cuh / ps_mergeutil.cuh, the sources the kernel is built from.)
+#pragma once
+
+#include "ps_common.cuh"
+#include "ps_mergeutil.cuh"
+
+namespace ps {
+
+// ---------------------------------------------------------------------------------------
+// One level pass: all merges of the tree nodes at one depth whose ranges exceed the subtree
+// limit, split into output tiles that start at the node's lo and then at the multiples of the
+// tile size (IPT outputs per consumer thread x 256 threads) inside it.  Persistent and warp-specialized:
+//  * CTA b owns the contiguous tile range [b*T/G, (b+1)*T/G) of the pass (T tiles, G CTAs), so
+//    the co-rank at the end of one tile is the co-rank at the start of the next;
+//  * warp 8 (producer) walks the CTA's tiles: it finds each tile's end co-rank with a 32-way
+//    warp search inside the window the start co-rank allows (at most one tile wide; its
+//    probes touch the lines the tile's copy then reads), waits for a free stage, and issues the
+//    tile's four bulk copies (left/right keys and payloads, 16-byte aligned chunks) on that
+//    stage's "full" mbarrier;
+//  * warps 0-7 (consumers) wait for a full stage, merge its IPT outputs per thread
+//    (co-rank inside shared memory, then a serial stable merge), write them with 128-bit
+//    stores, and release the stage on its "empty" mbarrier.
+// A ring of NS stages: the copies of the next NS-1 tiles overlap the merge of the current one.
+// All waits are bounded; a timeout posts kDevTimeout and the CTA drains its copies and exits.
+// ---------------------------------------------------------------------------------------
+constexpr int kPassThreads = kMergeThreads + 32;  // 8 consumer warps + 1 producer warp
+
+struct StageDesc {
+  int32_t g0, g1, i0, i1;   // outputs [g0, g1); left elements [i0, i1) of the node
+  int32_t lo, mid, la, lb;  // node [lo, mid) + [mid, hi)
+  int32_t aoff, boff, vaoff, vboff;  // smem element offsets of A[i0], B[j0] (keys / payloads)
+  int32_t pad[4];
+};
+
+template <class K, bool V, int NS, int IPT>
+struct PassLayout {
+  typedef typename K::T T;
+  static constexpr int kStages = NS;
+  static constexpr int kTile = IPT * kMergeThreads;
+  static constexpr int KU = 16 / (int)sizeof(T);
+  static constexpr int KCAP = kTile + 4 * KU;
+  static constexpr int VCAP = kTile + 16;
+  static constexpr size_t kKeyBytes = ((size_t)KCAP * sizeof(T) + 127) & ~(size_t)127;
+  static constexpr size_t kValBytes = V ? (((size_t)VCAP * 4 + 127) & ~(size_t)127) : 0;
+  static constexpr size_t kStageBytes = kKeyBytes + kValBytes;
+  static constexpr size_t kBarOff = 0;  // full[NS], empty[NS]
+  static constexpr size_t kDescOff = (2 * NS * 8 + 63) & ~(size_t)63;  // StageDesc[NS]
+  static constexpr size_t kFlagOff = kDescOff + NS * sizeof(StageDesc);
+  static constexpr size_t kStageOff = (kFlagOff + 16 + 127) & ~(size_t)127;
+  static constexpr size_t kBytes = kStageOff + NS * kStageBytes;
+};
+
+// smallest i in [a, b] with i == b or A[i] > B[diag-1-i], by a 32-way warp search in global memory
+template <class K>
+__device__ __forceinline__ int32_t warp_corank(const typename K::T* __restrict__ A, const typename K::T* __restrict__ B,
+                                               int32_t diag, int32_t a, int32_t b) {
+  const int lane = threadIdx.x & 31;
+  while (a < b) {
+    const int32_t span = b - a;
+    const int32_t x = a + (int32_t)(((int64_t)span * lane) >> 5);  // probes in [a, b)
+    const bool gt = !key_le<K>(A[x], B[diag - 1 - x]);
+    const uint32_t mask = __ballot_sync(0xffffffffu, gt);
+    if (mask) {
+      const int fl = __ffs(mask) - 1;
+      const int32_t xf = __shfl_sync(0xffffffffu, x, fl);
+      const int32_t xp = __shfl_sync(0xffffffffu, x, fl > 0 ? fl - 1 : 0);
+      b = xf;
+      if (fl > 0) a = xp + 1;
+    } else {
+      a = __shfl_sync(0xffffffffu, x, 31) + 1;
+    }
+  }
+  return a;
+}
+
+// AND of a predicate over the kMergeThreads consumer threads (also a barrier among them)
+__device__ __forceinline__ bool consumer_all(bool p) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred a, b;\n setp.ne.u32 a, %1, 0;\n bar.red.and.pred b, 1, %2, a;\n selp.u32 %0, 1, 0, b;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)p), "n"(kMergeThreads)
+      : "memory");
+  return r != 0;
+}
+
+// Element range [e0, e1) of base widened to whole 16-byte blocks: [c0, c1) (element indices,
+// possibly c0 < 0 by a few elements when base itself is not 16-byte aligned).  Empty ranges give
+// an empty chunk.  Needs base aligned to sizeof(E).
+template <class E>
+__device__ __forceinline__ void chunk16(const E* base, int32_t e0, int32_t e1, int32_t& c0, int32_t& c1) {
+  constexpr int kPer = 16 / (int)sizeof(E);
+  const int32_t phase = (int32_t)(((uintptr_t)base & 15u) / sizeof(E));  // elements before base in its block
+  c0 = ((e0 + phase) & ~(kPer - 1)) - phase;
+  c1 = (e1 > e0) ? (((e1 + phase + kPer - 1) & ~(kPer - 1)) - phase) : c0;
+}
+
+__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t tries = 0;
+  while (!mbar_try_wait(bar, parity))
+    if (++tries > kMbarTries) return false;
+  return true;
+}
+
+// CTAs per SM the register budget is sized for (16 items per thread need more registers).
+__host__ __device__ constexpr int pass_min_blocks(int ipt) { return ipt <= 12 ? 4 : 3; }
+
+template <class K, bool V, int NS, int IPT>
+__global__ void __launch_bounds__(kPassThreads, pass_min_blocks(IPT))
+level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __restrict__ srcv,
+                  typename K::T* __restrict__ dstk, uint32_t* __restrict__ dstv,
+                  const int4* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
+                  uint32_t ntiles, const unsigned long long* __restrict__ ctr, uint32_t cap,
+                  PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+  typedef typename K::T T;
+  typedef PassLayout<K, V, NS, IPT> Lay;
+  constexpr int kTile = Lay::kTile;
+  if (ctr != nullptr) {  // counts from the plan on the device (no host round trip)
+    if (hdr->status & kDevBadOffsets) return;
+    const unsigned long long v = *ctr;
+    nitems = (uint32_t)(v >> 32);
+    ntiles = (uint32_t)(v & 0xffffffffull);
+    if (nitems > cap) return;  // the plan posted an internal error already
+  }
+  constexpr int KU = Lay::KU;
+  constexpr int kPassStages = NS;
+  extern __shared__ __align__(128) uint8_t smem[];
+  uint64_t* full = (uint64_t*)(smem + Lay::kBarOff);
+  uint64_t* empty = full + kPassStages;
+  StageDesc* sdesc = (StageDesc*)(smem + Lay::kDescOff);
+  volatile int32_t* abort_flag = (volatile int32_t*)(smem + Lay::kFlagOff);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  if (t_begin >= t_end) return;  // no tile for this CTA (uniform over the CTA)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kPassStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kMergeThreads / 32);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  if (warp == kMergeThreads / 32) {
+    // ------------------------------ producer ------------------------------
+    int32_t slot = 0;
+    if (lane == 0) slot = slot_of_tile(tile_off, nitems, t_begin);
+    slot = __shfl_sync(0xffffffffu, slot, 0);
+    int4 nd = nodes[slot];  // lo, mid, hi, boundary
+    int32_t la = nd.y - nd.x, lb = nd.z - nd.y;
+    const T* A = srck + nd.x;
+    const T* B = srck + nd.y;
+    const int32_t k0 = (int32_t)(t_begin - tile_off[slot]);
+    int32_t g0 = (k0 == 0) ? nd.x : (nd.x / kTile + k0) * kTile;
+    int32_t i0 = 0;
+    if (g0 > nd.x) {
+      const int32_t diag = g0 - nd.x;
+      i0 = warp_corank<K>(A, B, diag, max(0, diag - lb), min(diag, la));
+    }
+    // Tiles go out in batches of kSearchBatch: lane group m (8 lanes) finds the end co-rank of
+    // the batch's tile m with an 8-way search, all groups at once.  Each window is anchored at
+    // the last co-rank known in the same node (the batch start, or 0 at a node's first tile),
+    // so it is at most kSearchBatch tiles wide.
+    constexpr int kSearchBatch = 4;
+    const int grp = lane >> 3, gl = lane & 7;
+    const uint32_t gmask = 0xFFu << (grp * 8);
+    uint32_t issued = 0;
+    bool ok = true;
+    uint32_t t = t_begin;
+    while (t < t_end && ok) {
+      const int nb = (int)min((uint32_t)kSearchBatch, t_end - t);
+      int4 m_nd[kSearchBatch];
+      int32_t m_g0[kSearchBatch], m_g1[kSearchBatch], m_slot[kSearchBatch], m_a[kSearchBatch], m_b[kSearchBatch];
+      bool m_new[kSearchBatch];
+      {
+        int32_t cs = slot, cg0 = g0, ag = g0, ai = i0;
+        int4 cnd = nd;
+#pragma unroll
+        for (int m = 0; m < kSearchBatch; ++m) {
+          m_new[m] = false;
+          if (m < nb) {
+            const uint32_t tt = t + m;
+            if (cs + 1 < (int32_t)nitems && tile_off[cs + 1] <= tt) {
+              while (cs + 1 < (int32_t)nitems && tile_off[cs + 1] <= tt) ++cs;
+              cnd = nodes[cs];
+              cg0 = cnd.x;
+              ag = cnd.x;
+              ai = 0;
+              m_new[m] = true;
+            }
+            const int32_t g1 = min(cnd.z, (cg0 / kTile + 1) * kTile);
+            const int32_t cla = cnd.y - cnd.x, clb = cnd.z - cnd.y, diag = g1 - cnd.x;
+            m_nd[m] = cnd;
+            m_slot[m] = cs;
+            m_g0[m] = cg0;
+            m_g1[m] = g1;
+            // window of the end co-rank (empty window when the tile ends at the node's end)
+            m_a[m] = (g1 < cnd.z) ? max(ai, diag - clb) : cla;
+            m_b[m] = (g1 < cnd.z) ? min(ai + (g1 - ag), cla) : cla;
+            cg0 = g1;
+          }
+        }
+      }
+      // group grp searches tile grp (8-way probes)
+      int32_t res = 0;
+      {
+        int4 snd = m_nd[0];
+        int32_t sa = m_a[0], sb = m_b[0], sg1 = m_g1[0];
+#pragma unroll
+        for (int m = 1; m < kSearchBatch; ++m)
+          if (grp == m) {
+            snd = m_nd[m];
+            sa = m_a[m];
+            sb = m_b[m];
+            sg1 = m_g1[m];
+          }
+        if (grp < nb) {
+          const T* GA = srck + snd.x;
+          const T* GB = srck + snd.y;
+          const int32_t diag = sg1 - snd.x;
+          int32_t ga = sa, gb = sb;
+          while (ga < gb) {
+            const int32_t span = gb - ga;
+            const int32_t x = ga + (int32_t)(((int64_t)span * gl) >> 3);
+            const bool gt = !key_le<K>(GA[x], GB[diag - 1 - x]);
+            const uint32_t msk = (__ballot_sync(gmask, gt) >> (grp * 8)) & 0xFFu;
+            if (msk) {
+              const int fl = __ffs(msk) - 1;
+              const int32_t xf = __shfl_sync(gmask, x, grp * 8 + fl);
+              const int32_t xp = __shfl_sync(gmask, x, grp * 8 + (fl > 0 ? fl - 1 : 0));
+              gb = xf;
+              if (fl > 0) ga = xp + 1;
+            } else {
+              ga = __shfl_sync(gmask, x, grp * 8 + 7) + 1;
+            }
+          }
+          res = ga;
+        }
+      }
+      int32_t m_i1[kSearchBatch];
+#pragma unroll
+      for (int m = 0; m < kSearchBatch; ++m) m_i1[m] = __shfl_sync(0xffffffffu, res, m * 8);
+      // issue the batch in order
+#pragma unroll
+      for (int m = 0; m < kSearchBatch; ++m) {
+        if (m < nb && ok) {
+          const int4 cnd = m_nd[m];
+          const int32_t cla = cnd.y - cnd.x;
+          const int32_t tg0 = m_g0[m], tg1 = m_g1[m];
+          const int32_t ti0 = m_new[m] ? 0 : (m == 0 ? i0 : m_i1[m - 1]);
+          const int32_t ti1 = (tg1 < cnd.z) ? m_i1[m] : cla;
+          const int s = (int)(issued % kPassStages);
+          const uint32_t use = issued / kPassStages;
+          if (!__all_sync(0xffffffffu, bounded_wait(&empty[s], (use & 1u) ^ 1u))) {
+            ok = false;
+          } else {
+            if (lane == 0) {
+              const int32_t a0 = cnd.x + ti0, a1 = cnd.x + ti1;
+              const int32_t b0 = cnd.y + (tg0 - cnd.x - ti0), b1 = cnd.y + (tg1 - cnd.x - ti1);
+              // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only
+              // need natural alignment; a chunk may start up to 15 bytes before a range and end up
+              // to 15 bytes after it, always inside 16-byte blocks holding range elements)
+              int32_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
+              chunk16(srck, a0, a1, ka0, ka1);
+              chunk16(srck, b0, b1, kb0, kb1);
+              chunk16(srcv, a0, a1, va0, va1);
+              chunk16(srcv, b0, b1, vb0, vb1);
+              StageDesc d;
+              d.g0 = tg0;
+              d.g1 = tg1;
+              d.i0 = ti0;
+              d.i1 = ti1;
+              d.lo = cnd.x;
+              d.mid = cnd.y;
+              d.la = cla;
+              d.lb = cnd.z - cnd.y;
+              d.aoff = a0 - ka0;
+              d.boff = (ka1 - ka0) + (b0 - kb0);
+              d.vaoff = a0 - va0;
+              d.vboff = (va1 - va0) + (b0 - vb0);
+              sdesc[s] = d;
+              uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
+              T* sk = (T*)stage;
+              uint32_t* sv = (uint32_t*)(stage + Lay::kKeyBytes);
+              const uint32_t kba = (uint32_t)(ka1 - ka0) * sizeof(T), kbb = (uint32_t)(kb1 - kb0) * sizeof(T);
+              const uint32_t vba = V ? (uint32_t)(va1 - va0) * 4u : 0u, vbb = V ? (uint32_t)(vb1 - vb0) * 4u : 0u;
+              mbar_arrive_expect_tx(&full[s], kba + kbb + vba + vbb);
+              if (kba) bulk_g2s(sk, srck + ka0, kba, &full[s]);
+              if (kbb) bulk_g2s(sk + (ka1 - ka0), srck + kb0, kbb, &full[s]);
+              if (V) {
+                if (vba) bulk_g2s(sv, srcv + va0, vba, &full[s]);
+                if (vbb) bulk_g2s(sv + (va1 - va0), srcv + vb0, vbb, &full[s]);
+              }
+            }
+            __syncwarp();
+            ++issued;
+          }
+        }
+      }
+      // carry the state to the next batch: next tile starts where the batch's last tile ended
+      slot = m_slot[0];
+      nd = m_nd[0];
+      g0 = m_g1[0];
+      i0 = m_i1[0];
+#pragma unroll
+      for (int m = 1; m < kSearchBatch; ++m)
+        if (m < nb) {
+          slot = m_slot[m];
+          nd = m_nd[m];
+          g0 = m_g1[m];
+          i0 = (m_g1[m] < m_nd[m].z) ? m_i1[m] : (m_nd[m].y - m_nd[m].x);
+        }
+      if (nb == 1) i0 = (m_g1[0] < m_nd[0].z) ? m_i1[0] : (m_nd[0].y - m_nd[0].x);
+      t += nb;
+    }
+    if (!ok) {
+      if (lane == 0) post_status(&hdr->status, lib_status, kDevTimeout);
+      *abort_flag = 1;
+    }
+    // drain: every copy issued into a stage must have landed before the CTA exits
+    if (lane == 0) {
+      for (uint32_t q = (issued > kPassStages ? issued - kPassStages : 0); q < issued; ++q) {
+        const int s = (int)(q % kPassStages);
+        bounded_wait(&full[s], (q / kPassStages) & 1u);
+      }
+    }
+  } else {
+    // ------------------------------ consumers ------------------------------
+    const int tid = threadIdx.x;
+    uint32_t it = 0;
+    for (uint32_t t = t_begin; t < t_end; ++t, ++it) {
+      const int s = (int)(it % kPassStages);
+      const uint32_t use = it / kPassStages;
+      bool ready = false;
+      for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+        if (mbar_try_wait(&full[s], use & 1u)) {
+          ready = true;
+          break;
+        }
+        if (*abort_flag) break;
+      }
+      // all consumers take the same branch (they meet at named barriers below)
+      if (!consumer_all(ready)) {
+        if (tid == 0 && !*abort_flag) post_status(&hdr->status, lib_status, kDevTimeout);
+        break;
+      }
+      const StageDesc d = sdesc[s];
+      const uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
+      const T* A = (const T*)stage + d.aoff;
+      const T* B = (const T*)stage + d.boff;
+      const uint32_t* sv = (const uint32_t*)(stage + Lay::kKeyBytes);
+      const int32_t len = d.g1 - d.g0, la = d.i1 - d.i0, lb = len - la;
+      const int32_t diag = tid * IPT;
+      if (diag < len) {
+        int32_t i = corank_serial<K>(A, B, la, lb, diag);
+        int32_t j = diag - i;
+        const int32_t cnt = min(IPT, len - diag);
+        T key[IPT];
+        uint32_t val[IPT];
+        // heads of both inputs stay in registers: one shared-memory key read per output
+        T a = A[min(i, la - 1 >= 0 ? la - 1 : 0)], b = B[min(j, lb - 1 >= 0 ? lb - 1 : 0)];
+        if (cnt == IPT) {
+#pragma unroll
+          for (int q = 0; q < IPT; ++q) {
+            const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
+            key[q] = takeA ? a : b;
+            if (V) val[q] = sv[takeA ? d.vaoff + i : d.vboff + j];
+            i += takeA ? 1 : 0;
+            j += takeA ? 0 : 1;
+            if (takeA) {
+              if (i < la) a = A[i];
+            } else {
+              if (j < lb) b = B[j];
+            }
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < IPT; ++q) {
+            if (q < cnt) {
+              const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
+              key[q] = takeA ? a : b;
+              if (V) val[q] = sv[takeA ? d.vaoff + i : d.vboff + j];
+              i += takeA ? 1 : 0;
+              j += takeA ? 0 : 1;
+              if (takeA) {
+                if (i < la) a = A[i];
+              } else {
+                if (j < lb) b = B[j];
+              }
+            }
+          }
+        }
+        const int32_t g = d.g0 + diag;
+        if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
+          uint4* o = (uint4*)(dstk + g);
+#pragma unroll
+          for (int q = 0; q < IPT / KU; ++q) {
+            uint4 w;
+            T* wt = (T*)&w;
+#pragma unroll
+            for (int u = 0; u < KU; ++u) wt[u] = key[q * KU + u];
+            o[q] = w;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < IPT; ++q)
+            if (q < cnt) dstk[g + q] = key[q];
+        }
+        if (V) {
+          if (cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
+            uint4* o = (uint4*)(dstv + g);
+#pragma unroll
+            for (int q = 0; q < IPT / 4; ++q)
+              o[q] = make_uint4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+          } else {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q)
+              if (q < cnt) dstv[g + q] = val[q];
+          }
+        }
+      }
+      __syncwarp();
+      if ((tid & 31) == 0) mbar_arrive(&empty[s]);
+    }
+  }
+}
+
+}  // namespace ps
