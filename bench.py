@@ -54,6 +54,21 @@ def _peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time (every rank gets it): the whole job is done when the last replica is."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, n: int, steps: int, max_ms: float) -> float:
+    """Whole-job GKeys/s of `world` replicas that each sorted `steps` arrays of n keys."""
+    return world * n * steps / (max_ms / 1000.0) / 1e9
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -455,12 +470,9 @@ def run_gpu(args):
     # correctness of the timed outputs (cheap device-side checks on the last copy)
     k, v = copies[(args.steps - 1) % ncopies]
     ok = bool((k[1:] >= k[:-1]).all().item())
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
-    value = ws * n * args.steps / (total_ms / 1000.0) / 1e9
+    value = replica_throughput(ws, n, args.steps, total_ms)
 
     peak, peak_kind = _peaks()
     mt = prof["level_pass"]
@@ -546,11 +558,7 @@ def run_gpu(args):
             streams[0].wait_event(ev)
         e1.record(streams[0])
         torch.cuda.synchronize(dev)
-        e2e_ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
+        e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         ok_e2e = all(bool(np.all(o[0].numpy()[1:] >= o[0].numpy()[:-1])) for o in outs)
         # serial: one ps_sort_host call at a time (synchronous, pool workspace)
         hk_out, hv_out = outs[0]
@@ -567,7 +575,7 @@ def run_gpu(args):
         s1.record(stream)
         torch.cuda.synchronize(dev)
         serial_ms = s0.elapsed_time(s1) / serial_steps
-        line["e2e"] = {"value": ws * n * e2e_steps / (e2e_ms / 1000.0) / 1e9, "unit": UNIT,
+        line["e2e"] = {"value": replica_throughput(ws, n, e2e_steps, e2e_ms), "unit": UNIT,
                        "h2d_bytes_per_step": n * eb, "d2h_bytes_per_step": n * eb, "steps": e2e_steps,
                        "ms_per_step": e2e_ms / e2e_steps,
                        "entry": "ps_sort_host_ws on 3 streams (pinned host buffers, one device buffer set per stream)",
@@ -630,11 +638,38 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--batched-segments", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=300)
+    ap.add_argument("--once", choices=["runs", "perm"], default=None,
+                    help="profiling driver: exactly one ps_sort_ws of the headline (runs) or permutation "
+                         "workload at --n, no warm-up, no JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
+    if args.once:
+        return run_once(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
+
+
+def run_once(args):
+    """One sort and nothing else, so that a profiler's launch list is exactly one pipeline."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1805_04154_gb300 import _build
+    _build.build()
+    import paper_1805_04154_gb300 as ps
+    ps.load()
+    n = args.n
+    keys, vals = _gen(n, SEED) if args.once == "runs" else workloads.perm_i32(n, seed=SEED)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n), dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
+    torch.cuda.synchronize()
+    ok = ps.ps_stream_status() == 0 and bool((dk[1:] >= dk[:-1]).all().item())
+    print(f"once {args.once} n={n} sorted={ok}")
+    return 0 if ok else 1
 
 
 if __name__ == "__main__":
