@@ -1,9 +1,9 @@
 """Continuous-batching sort service on one GPU.
 
 Requests (host tensors of keys, optional 32-bit payload) are packed back to back into one of a
-few fixed device arena slots and sorted by a single ``ps_sort_segmented_ws`` call per slot (each
-request is one segment, so each result is exactly what ``ps_sort`` gives for that request
-alone).  The slots rotate through three CUDA streams, so the host-to-device copies of one batch,
+few fixed device arena slots and sorted by a single device-driven segmented call
+(``ps_sort_async_ws``, no host round trip) per slot (each request is one segment, so each result
+is exactly what ``ps_sort`` gives for that request alone).  The slots rotate through three CUDA streams, so the host-to-device copies of one batch,
 the sort of another and the device-to-host copies of a third overlap on the GPU; a request that
 arrives while earlier batches are on the GPU joins the next batch as soon as a slot frees up.
 
@@ -131,11 +131,14 @@ class SortServer:
         return r
 
     def drain(self, timeout: float | None = None) -> None:
-        """Wait until every submitted request is done."""
+        """Wait until every submitted request is done; raise if the device reported an error for
+        any batch since the last drain (the sorts run without host round trips, so device-side
+        errors are collected here)."""
         with self._cv:
             ok = self._cv.wait_for(lambda: self._outstanding == 0, timeout)
         if not ok:
             raise TimeoutError("server did not drain")
+        _check(load().ps_stream_status(ctypes.c_void_p(self.compute.cuda_stream)), "SortServer batch")
 
     def close(self) -> None:
         with self._cv:
@@ -188,12 +191,14 @@ class SortServer:
             h2d_done = torch.cuda.Event()
             h2d_done.record(self.h2d)
         self.compute.wait_event(h2d_done)
-        st = load().ps_sort_segmented_ws(self.kt, ctypes.c_void_p(slot.dk.data_ptr()),
-                                         None if slot.dv is None else ctypes.c_void_p(slot.dv.data_ptr()), n,
-                                         ctypes.c_void_p(slot.doff.data_ptr()), count,
-                                         ctypes.c_void_p(slot.ws.data_ptr()), slot.ws.numel(),
-                                         ctypes.c_void_p(self.compute.cuda_stream))
-        _check(st, "ps_sort_segmented_ws")
+        # device-driven segmented sort: queued without a host round trip, so this thread goes on
+        # to the next batch while the GPU copies and sorts this one
+        st = load().ps_sort_async_ws(self.kt, ctypes.c_void_p(slot.dk.data_ptr()),
+                                     None if slot.dv is None else ctypes.c_void_p(slot.dv.data_ptr()), n,
+                                     ctypes.c_void_p(slot.doff.data_ptr()), count, 0,
+                                     ctypes.c_void_p(slot.ws.data_ptr()), slot.ws.numel(),
+                                     ctypes.c_void_p(self.compute.cuda_stream))
+        _check(st, "ps_sort_async_ws")
         sort_done = torch.cuda.Event()
         sort_done.record(self.compute)
         self.d2h.wait_event(sort_done)
