@@ -150,6 +150,13 @@ size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segment
 ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
                           int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
 
+/* Failure-path self-test (no fault, trap or hang): queues one warp that waits on a
+ * shared-memory mbarrier nothing completes, polling it at most `polls` times with the same
+ * bounded loop the merge kernels use; when the polls run out it posts the timeout bit to the
+ * library's status word and returns.  ps_stream_status(stream) then reports PS_ERR_TIMEOUT (and
+ * clears it), and the device stays usable. */
+ps_status ps_selftest_wait_timeout(uint32_t polls, void* stream);
+
 /* Level-pass configuration and its autotuner.  A level pass splits its merges into tiles of
  * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
  * shared-memory buffers; the library carries the configurations (12, 2), (12, 3), (12, 4),

@@ -91,6 +91,7 @@ def load():
                 "ps_autotune": ([i32, vp, vp, i64, vp, vp], i32),
                 "ps_tune_set": ([i32, i32, i32, i32], i32),
                 "ps_tune_get": ([i32, i32, vp, vp], i32),
+                "ps_selftest_wait_timeout": ([ctypes.c_uint32, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
@@ -380,3 +381,11 @@ def ps_tune_get(key_type: int, has_vals: bool) -> tuple[int, int]:
     a, b = ctypes.c_int(0), ctypes.c_int(0)
     _check(load().ps_tune_get(key_type, 1 if has_vals else 0, ctypes.byref(a), ctypes.byref(b)), "ps_tune_get")
     return a.value, b.value
+
+
+def ps_selftest_wait_timeout(polls: int = 1 << 14, stream=None) -> None:
+    """Queue the bounded-wait self-test (see include/powersort.h); then ps_stream_status()
+    reports PS_ERR_TIMEOUT."""
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(load().ps_selftest_wait_timeout(int(polls), ctypes.c_void_p(stream.cuda_stream)), "ps_selftest_wait_timeout")

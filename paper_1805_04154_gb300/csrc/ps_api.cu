@@ -10,6 +10,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "powersort.h"
 #include "ps_internal.h"
 
@@ -146,15 +148,24 @@ std::vector<ProfRec> g_prof_pending;
 double g_prof_ms[kStages] = {};
 uint64_t g_prof_launch[kStages] = {}, g_prof_bytes[kStages] = {};
 
+// Stage scopes: an NVTX range on the host (visible to Nsight tools; inert without one) and,
+// while profiling is enabled, CUDA events on the stream around the stage's launches.
+const char* const kStageNames[kStages] = {"ps:detect", "ps:meta", "ps:subtree_smem", "ps:leaf_place",
+                                          "ps:unused", "ps:level_pass", "ps:stage6", "ps:stage7"};
+
 struct StageTimer {
   int stage;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   bool on;
   StageTimer(int st, cudaStream_t strm) : stage(st), s(strm), on(g_prof_on.load() != 0) {
+    nvtxRangePushA(kStageNames[st]);
     if (on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
     else on = false;
   }
+  ~StageTimer() { nvtxRangePop(); }
+  StageTimer(const StageTimer&) = delete;
+  StageTimer& operator=(const StageTimer&) = delete;
   void done(uint64_t bytes, uint64_t launches) {
     g_launches += launches;
     if (!on) return;
@@ -609,6 +620,16 @@ ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d
   const bool seg = d_offsets != nullptr;
   return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
              workspace_bytes, (cudaStream_t)stream, &an);
+}
+
+ps_status ps_selftest_wait_timeout(uint32_t polls, void* stream) {
+  int dev = 0;
+  PS_TRY(cudaGetDevice(&dev));
+  uint32_t* w = lib_status_word(dev);
+  if (!w) return PS_ERR_CUDA;
+  PS_TRY(launch_wait_timeout_probe(polls, w, (cudaStream_t)stream));
+  g_launches += 1;
+  return PS_OK;
 }
 
 ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages) {

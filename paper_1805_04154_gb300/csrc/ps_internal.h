@@ -83,5 +83,6 @@ cudaError_t launch_entropy(const Ctx& c, double* d_out);
 cudaError_t launch_check_offsets(const Ctx& c);
 cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped);
 cudaError_t launch_status_out(const Ctx& c);
+cudaError_t launch_wait_timeout_probe(uint32_t polls, uint32_t* lib_status, cudaStream_t s);
 
 }  // namespace ps

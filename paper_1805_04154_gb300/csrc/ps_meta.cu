@@ -1,6 +1,7 @@
 // Stages 2-3 and planning: node powers, the merge tree as nearest smaller values of the powers,
 // node/leaf depths, merge cost, and the work lists of stage 4.  Key-independent; O(r) work.
 #include "ps_internal.h"
+#include "ps_level.cuh"
 
 namespace ps {
 
@@ -646,6 +647,27 @@ __global__ void status_out_kernel(const PlanHeader* __restrict__ hdr, uint32_t* 
 
 cudaError_t launch_status_out(const Ctx& c) {
   status_out_kernel<<<1, 32, 0, c.stream>>>(c.hdr, c.lib_status);
+  return cudaGetLastError();
+}
+
+// Failure-path self-test: one warp waits on a shared-memory mbarrier that nothing completes --
+// what a level pass's consumers would see if a stage's copies never landed -- with the same
+// bounded poll loop; it gives up after `polls` polls, posts kDevTimeout to the library's status
+// word and returns, so the context stays usable.
+__global__ void wait_timeout_probe_kernel(uint32_t polls, uint32_t* lib_status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  bool done = false;
+  for (uint32_t t = 0; t < polls && !done; ++t) done = mbar_try_wait(&bar, 0);
+  if (!__all_sync(0xffffffffu, done) && threadIdx.x == 0) post_status(nullptr, lib_status, kDevTimeout);
+}
+
+cudaError_t launch_wait_timeout_probe(uint32_t polls, uint32_t* lib_status, cudaStream_t s) {
+  wait_timeout_probe_kernel<<<1, 32, 0, s>>>(polls, lib_status);
   return cudaGetLastError();
 }
 

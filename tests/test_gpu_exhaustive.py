@@ -1,0 +1,125 @@
+"""Exhaustive small cases on the GPU, all in one segmented call each, against the CPU oracle:
+every pattern of adjacent relations (<, =, >) for 2 <= n <= 8 (3^(n-1) arrays per n) and every
+composition of 12 into run lengths (2^11 arrays, ascending runs separated by drops, plain and
+with descending runs) -- output and payload bit-exact, run starts, directions, node powers, leaf
+depths and merge cost equal.  Plus structural properties of the device tree: powers in
+[1, floor(lg n_seg) + 1], adjacent powers differ, a node's parent has the smaller power, and on
+random permutations powersort's and peeksort's merge costs are within 1.5% of each other."""
+import itertools
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ps():
+    import paper_1805_04154_gb300 as ps
+    from paper_1805_04154_gb300 import _build
+    _build.build()
+    ps.load()
+    return ps
+
+
+def _relation_arrays():
+    rng = np.random.default_rng(5)
+    arrays = []
+    for n in range(2, 9):
+        for pat in itertools.product((-1, 0, 1), repeat=n - 1):
+            steps = np.array(pat, np.int64) * rng.integers(1, 4, size=n - 1)
+            arrays.append(np.concatenate([[0], np.cumsum(steps)]).astype(np.int32))
+    return arrays
+
+
+def _composition_arrays():
+    arrays = []
+    for cuts in itertools.product((0, 1), repeat=11):
+        lens, cur = [], 1
+        for c in cuts:
+            if c:
+                lens.append(cur)
+                cur = 1
+            else:
+                cur += 1
+        lens.append(cur)
+        for desc in (False, True):
+            parts, base = [], 1000
+            for k, L in enumerate(lens):
+                run = np.arange(base, base + L, dtype=np.int32)
+                if desc and k % 2:
+                    run = run[::-1].copy()
+                parts.append(run)
+                base -= 50  # every run starts below the previous one
+            arrays.append(np.concatenate(parts))
+    return arrays
+
+
+def _check_batch(ps, arrays):
+    off = np.zeros(len(arrays) + 1, np.int64)
+    off[1:] = np.cumsum([a.size for a in arrays])
+    keys = np.concatenate(arrays).astype(np.int32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    ref = oracle.sort_segmented(keys, vals, off)
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    doff = torch.from_numpy(off).cuda()
+    an = ps.ps_analyze(dk, offsets=doff, key_type=0)
+    np.testing.assert_array_equal(an["starts"], ref[2])
+    np.testing.assert_array_equal(an["desc"], ref[3])
+    np.testing.assert_array_equal(an["power"].astype(np.int32), ref[4])
+    np.testing.assert_array_equal(an["leaf_depth"].astype(np.int32), ref[5])
+    assert an["cost"] == ref[6]
+    ps.ps_sort_segmented(dk, dv, doff, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
+    return an, off
+
+
+def test_all_relation_patterns(ps):
+    _check_batch(ps, _relation_arrays())
+
+
+def test_all_compositions_of_12(ps):
+    _check_batch(ps, _composition_arrays())
+
+
+def test_tree_structure_properties(ps):
+    keys, vals, off = workloads.segmented_i32(200, seed=17, lo_exp=1, hi_exp=16)
+    an, _ = _check_batch(ps, [keys[a:b] for a, b in zip(off[:-1], off[1:])])
+    S, P, L, R = an["starts"], an["power"].astype(np.int64), an["node_left"], an["node_right"]
+    seg_of_run = np.searchsorted(off, S[:-1], side="right") - 1
+    for j in range(1, an["runs"]):
+        if seg_of_run[j] != seg_of_run[j - 1]:
+            assert P[j] == 0  # segment border
+            continue
+        s = seg_of_run[j]
+        n_seg = int(off[s + 1] - off[s])
+        assert 1 <= P[j] <= int(np.floor(np.log2(n_seg))) + 1
+        assert P[j] != P[j - 1] or P[j - 1] == 0
+        par = L[j] if P[L[j]] > P[R[j]] else R[j]
+        assert P[par] < P[j]
+
+
+def test_permutation_costs_of_both_trees_agree(ps):
+    keys, _ = workloads.perm_i32(1 << 20, seed=23)
+    dk = torch.from_numpy(keys).cuda()
+    c_pow = ps.ps_analyze(dk, key_type=0)["cost"]
+    c_peek = ps.ps_analyze(dk, key_type=0, tree=ps.PS_TREE_PEEKSORT)["cost"]
+    assert abs(c_pow - c_peek) / c_pow < 0.015
+
+
+def test_bounded_wait_timeout_reported_and_device_usable(ps):
+    ps.ps_selftest_wait_timeout(1 << 12)
+    assert ps.ps_stream_status() == 5  # PS_ERR_TIMEOUT, then cleared
+    assert ps.ps_stream_status() == 0
+    keys, vals = workloads.runs_i32(50001, seed=3)
+    ref = oracle.powersort(keys, vals)
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    ps.ps_sort(dk, dv, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
