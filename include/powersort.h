@@ -206,6 +206,26 @@ ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64
                           int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
                           int32_t* node_right, uint8_t* node_depth, void* stream);
 
+/* Minimal run length (Sec. 5.1: the tuned implementations extend every run shorter than
+ * w = 24 by insertion sort to w elements, capped at the end of the array).  Runs are found left
+ * to right as in ExtendRunRight of Alg. 2, but a run [s, e) with e - s < min_run becomes
+ * [s, min(s + min_run, end)) (end = n, or the end of its segment); the next run starts there.
+ * Such an extended run is sorted stably when it is placed (the order of key, then position: the
+ * result of reversing a strictly descending prefix and insertion-sorting the rest), and the
+ * powersort tree (Alg. 2) is built over the extended runs.  min_run = 1 is the plain greedy
+ * partition of every other entry point.
+ *   ps_sort_minrun_ws   as ps_sort_tree_ws with PS_TREE_POWERSORT (d_offsets NULL, count 1 for
+ *                       one array; workspace of ps_workspace_size bytes).
+ *   ps_analyze_minrun   as ps_analyze; desc[i] has bit 0 set if run i's first pair is strictly
+ *                       descending and bit 1 set if the run was extended.
+ * Errors as for those entry points, plus PS_ERR_INVALID_ARG for min_run outside [1, 32]. */
+ps_status ps_sort_minrun_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                            int64_t count, int min_run, void* workspace, size_t workspace_bytes, void* stream);
+ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
+                            int min_run, void* workspace, size_t workspace_bytes, int64_t* out_runs,
+                            uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
+                            int32_t* node_left, int32_t* node_right, uint8_t* node_depth, void* stream);
+
 /* Plan statistics of one array (keys on the device, not modified; workspace from the pool).
  * Synchronizes the stream. */
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream);

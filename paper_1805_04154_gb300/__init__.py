@@ -19,6 +19,7 @@ import torch
 __all__ = [
     "PowersortError", "PS_KEY_I32", "PS_KEY_U32", "PS_KEY_U64", "PS_KEY_F32", "lib_path", "load",
     "ps_sort", "ps_sort_ws", "ps_sort_segmented", "ps_sort_segmented_ws", "ps_workspace_size",
+    "ps_sort_minrun", "ps_sort_minrun_ws",
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
     "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
@@ -95,6 +96,9 @@ def load():
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
+                "ps_sort_minrun_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+                "ps_analyze_minrun": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                       vp], i32),
             }
             for name, (args, res) in sigs.items():
                 f = getattr(lib, name)
@@ -210,6 +214,30 @@ def ps_sort_tree(keys: torch.Tensor, vals: torch.Tensor | None = None, tree: int
     return keys
 
 
+def ps_sort_minrun_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor, min_run: int,
+                      offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> None:
+    """ps_sort_ws / ps_sort_segmented_ws with runs extended to ``min_run`` elements (Sec. 5.1)."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    n = keys.numel()
+    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
+        raise ValueError("vals must hold n 32-bit payloads")
+    seg = offsets is not None
+    _check(load().ps_sort_minrun_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                                    _dev_ptr(offsets, "offsets") if seg else None,
+                                    (offsets.numel() - 1) if seg else 1, int(min_run),
+                                    _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                    _stream_ptr(stream, keys.device)), "ps_sort_minrun_ws")
+
+
+def ps_sort_minrun(keys: torch.Tensor, vals: torch.Tensor | None = None, min_run: int = 24,
+                   offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> torch.Tensor:
+    """In-place stable sort with runs extended to ``min_run`` elements (workspace from PyTorch)."""
+    kt = key_type_of(keys) if key_type is None else key_type
+    ws = _workspace(ps_workspace_size(kt, vals is not None, keys.numel(), offsets is not None), keys.device)
+    ps_sort_minrun_ws(keys, vals, ws, min_run, offsets, kt, stream)
+    return keys
+
+
 def ps_sort_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: torch.Tensor,
                       key_type: int | None = None, stream=None) -> torch.Tensor:
     """Sort every segment [offsets[k], offsets[k+1]) on its own (offsets: CUDA int64, count+1)."""
@@ -244,10 +272,11 @@ def ps_merge_cost(run_lengths) -> int:
 
 
 def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type: int | None = None,
-               stream=None, tree: int = PS_TREE_POWERSORT) -> dict:
+               stream=None, tree: int = PS_TREE_POWERSORT, min_run: int = 1) -> dict:
     """Run detection, node powers (or peeksort's tree) and merge tree on the device (keys
     untouched); returns numpy arrays: starts, desc, power, leaf_depth, node_left, node_right,
-    node_depth, and runs, cost."""
+    node_depth, and runs, cost.  With ``min_run`` > 1 the runs are extended to that length
+    (powersort tree only) and desc carries bit 1 for extended runs."""
     kt = key_type_of(keys) if key_type is None else key_type
     n = keys.numel()
     seg = offsets is not None
@@ -259,11 +288,17 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
     runs = ctypes.c_int64(0)
     cost = ctypes.c_uint64(0)
     p = {k: ctypes.c_void_p(v.ctypes.data) for k, v in out.items()}
-    _check(load().ps_analyze_tree(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
-                                  (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(ws, "workspace"),
-                                  ws.numel(), ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"],
-                                  p["power"], p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
-                                  _stream_ptr(stream, keys.device)), "ps_analyze")
+    if min_run != 1:
+        if tree != PS_TREE_POWERSORT:
+            raise ValueError("min_run > 1 builds the powersort tree only")
+        fn, sel = load().ps_analyze_minrun, int(min_run)
+    else:
+        fn, sel = load().ps_analyze_tree, int(tree)
+    _check(fn(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
+              (offsets.numel() - 1) if seg else 1, sel, _dev_ptr(ws, "workspace"),
+              ws.numel(), ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"],
+              p["power"], p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
+              _stream_ptr(stream, keys.device)), "ps_analyze")
     r = int(runs.value)
     res = {"runs": r, "cost": int(cost.value), "starts": out["starts"][: r + 1].copy(),
            "desc": out["desc"][:r].copy(), "power": out["power"][: r + 1].copy(),

@@ -64,6 +64,14 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.thr_L = (uint64_t*)take(dthreads * 8);
   c.thr_F = segmented ? (uint64_t*)take(dthreads * 8) : nullptr;
   c.thr_fn = (uint32_t*)take(dthreads * 4);
+  {
+    // minimal-run-length tables (reserved always: about 0.02 bytes per element)
+    const size_t tiles = (size_t)std::max<int32_t>(c.detect_tiles, 1);
+    const size_t groups = (tiles + kMrGroup - 1) / kMrGroup;
+    c.mr_tile_tab = (uint32_t*)take(tiles * kMrStates * 4);
+    c.mr_grp_tab = (uint32_t*)take(groups * kMrStates * 4);
+    c.mr_grp_pre = (uint64_t*)take(groups * 8);
+  }
   const size_t tree_tiles = (size_t)(n + 1) / kTreeTile + 1;
   c.tree_stride = (int32_t)tree_tiles;
   c.tree_sum = (int32_t*)take(tree_tiles * 32 * 4);
@@ -290,10 +298,13 @@ ps_status read_plan_header(const Ctx& c, int dev, PlanHeader& h) {
 
 // The whole pipeline.  With `an` set, stops after planning and reports the plan instead.
 ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
-              bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an, int tree = 0) {
+              bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an, int tree = 0,
+              int min_run = 1) {
   ps_status st = check_args(kt, keys, vals, n);
   if (st != PS_OK) return st;
   if (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT) return PS_ERR_INVALID_ARG;
+  if (min_run < 1 || min_run > kMinRunMax) return PS_ERR_INVALID_ARG;
+  if (min_run > 1 && tree != PS_TREE_POWERSORT) return PS_ERR_UNSUPPORTED;
   if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
   if (n == 0 || (n == 1 && !an)) {
     if (an) {
@@ -322,6 +333,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
+  c.min_run = min_run;
   apply_pass_config(c, kt, vals != nullptr);
   const KeyLaunch* kl = launch_for(kt);
 
@@ -331,7 +343,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     StageTimer t(0, s);
     if (segmented) PS_TRY(launch_check_offsets(c));
     PS_TRY(kl->detect(c));
-    t.done((uint64_t)n * c.key_bytes, segmented ? 4 : 3);
+    t.done((uint64_t)n * c.key_bytes, (segmented ? 1 : 0) + (min_run > 1 ? 5 : 3));
   }
   {
     StageTimer t(1, s);
@@ -752,6 +764,23 @@ ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64
   const bool seg = d_offsets != nullptr;
   return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
              workspace_bytes, (cudaStream_t)stream, &an, tree);
+}
+
+ps_status ps_sort_minrun_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                            int64_t count, int min_run, void* workspace, size_t workspace_bytes, void* stream) {
+  const bool seg = d_offsets != nullptr;
+  return run(key_type, keys, vals, n, d_offsets, seg ? count : 1, seg, workspace, workspace_bytes,
+             (cudaStream_t)stream, nullptr, PS_TREE_POWERSORT, min_run);
+}
+
+ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
+                            int min_run, void* workspace, size_t workspace_bytes, int64_t* out_runs,
+                            uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
+                            int32_t* node_left, int32_t* node_right, uint8_t* node_depth, void* stream) {
+  AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
+  const bool seg = d_offsets != nullptr;
+  return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
+             workspace_bytes, (cudaStream_t)stream, &an, PS_TREE_POWERSORT, min_run);
 }
 
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream) {

@@ -1,0 +1,293 @@
+// Stage 1 with a minimal run length w (Sec. 5.1: the tuned implementations extend every run
+// shorter than w = 24 to w elements by insertion sort, capped at the end of the array).
+//
+// The run partition is the chain s_0 = 0, s_{i+1} = next(s_i) with
+//   next(s) = max(e, min(s + w, end))
+// where [s, e) is the greedy run from s (weakly ascending or strictly descending, ExtendRunRight
+// of Alg. 2) and `end` is the next forced start (a segment start or n).  A run is "extended"
+// when e < min(s + w, end); its elements are sorted stably when it is placed (ps_merge.cuh).
+// Every step advances by min(w, end - s) or more.
+//
+// As for w = 1 (ps_detect.cuh) the partition is found by a scan over transfer functions, now on
+// w + 2 states that describe the chain at a boundary b between two groups of positions:
+//   F(k), 0 <= k < w : the next run starts at b + k (or at an earlier forced start);
+//   A / D             : an ascending / descending run of length >= w is open at b and ends at
+//                       its first break at or after b.
+// A thread owns 32 positions and reads the pair and forced bits of the next 32 as a window, so
+// the end of any run it starts is either decided inside the window or the run is still open
+// after it (then its length is >= w and the exit state is A or D).  Exits of the form F(k) only
+// arise from extended runs or short natural runs, so k < w.
+//
+// Functions are kept as tables (exit state, run starts) per entry state; composition walks
+// them.  Kernels: reduce (tile tables) -> group (256-tile group tables) -> top (one thread walks
+// the groups) -> tile (entry state and run count of every tile) -> emit (threads replay their
+// runs from their entry states and write them at their ranks).  No block waits on another.
+#pragma once
+
+#include "ps_common.cuh"
+#include "ps_detect.cuh"
+
+namespace ps {
+
+// Table entries are exit state | run starts << 6: 16 bits for a thread (starts <= 32), 32 bits
+// for a tile or a group (starts <= 2^21).
+
+// Next run start after a run starting at window position pos (0 <= pos < 32).  Lw bit q: the
+// pair (p0+q-1, p0+q) is in order; Fw bit q: p0+q is a forced start or lies at or past n.
+// Returns the next start (64: the natural run is still open after the window) and the run's
+// flags: bit 0 = its first pair is strictly descending, bit 1 = extended to the minimal length.
+__device__ __forceinline__ int mr_next(uint64_t Lw, uint64_t Fw, int pos, int w, uint32_t& flags) {
+  const uint64_t fa = Fw & (~0ull << (pos + 1));
+  const int end = fa ? __ffsll((long long)fa) - 1 : 64;
+  int e;
+  uint32_t desc = 0;
+  if (end == pos + 1) {
+    e = pos + 1;  // the last position of a segment: a run of one element
+  } else {
+    const uint32_t asc = (uint32_t)(Lw >> (pos + 1)) & 1u;
+    desc = asc ^ 1u;
+    const uint64_t brk = ((asc ? ~Lw : Lw) | Fw) & (~0ull << (pos + 2));
+    e = brk ? __ffsll((long long)brk) - 1 : 64;
+  }
+  const int t = min(pos + w, end);
+  if (e >= t) {
+    flags = desc;
+    return e;
+  }
+  flags = 2u | desc;
+  return t;
+}
+
+// Exit state of a chain whose last run in this window ends at window position nx >= 32.
+__device__ __forceinline__ uint32_t mr_exit(int nx, uint32_t flags, int w) {
+  const int k = nx - 32;
+  if (k < w) return (uint32_t)k;  // the next start is fixed
+  return (flags & 1u) ? (uint32_t)w + 1u : (uint32_t)w;  // a long natural run is still open
+}
+
+// First run start in the window for entry state x, or -1 if an open run covers all 32 positions.
+__device__ __forceinline__ int mr_first(uint64_t Lw, uint64_t Fw, int w, uint32_t x) {
+  if (x < (uint32_t)w) {
+    const uint64_t fm = Fw & ((2ull << x) - 1ull);
+    return fm ? __ffsll((long long)fm) - 1 : (int)x;
+  }
+  const uint64_t brk = (((x == (uint32_t)w) ? ~Lw : Lw) | Fw) & 0xffffffffull;
+  return brk ? __ffsll((long long)brk) - 1 : -1;
+}
+
+// The thread's table entry for entry state x: exit state | run starts << 6.
+__device__ __forceinline__ uint32_t mr_walk(uint64_t Lw, uint64_t Fw, int nvalid, int w, uint32_t x) {
+  if (nvalid <= 0) return x;
+  int pos = mr_first(Lw, Fw, w, x);
+  if (pos < 0) return x;
+  uint32_t cnt = 0, ex = 0;
+  while (pos < nvalid) {
+    ++cnt;
+    uint32_t fl;
+    const int nx = mr_next(Lw, Fw, pos, w, fl);
+    if (nx >= 32) {
+      ex = mr_exit(nx, fl, w);
+      break;
+    }
+    pos = nx;
+  }
+  return ex | (cnt << 6);
+}
+
+// The window of one detection thread: its own pair / forced bits (positions 0..32) and those
+// of the next thread (positions 32..64); positions at or past n are marked forced (a stop).
+__device__ __forceinline__ void mr_window(uint64_t L, uint64_t F, uint64_t Ln, uint64_t Fn, int32_t p0, int32_t n,
+                                          uint64_t& Lw, uint64_t& Fw) {
+  Lw = (L & 0xffffffffull) | (Ln << 32);
+  Fw = (F & 0xffffffffull) | (Fn << 32);
+  const int64_t left = (int64_t)n - p0;
+  if (left < 64) Fw |= ~0ull << (left > 0 ? (int)left : 0);
+}
+
+// Compose one warp's 32 thread tables (shared memory, stride kMrStates) for entry states
+// lane and lane + 32; writes the warp table.
+__device__ __forceinline__ void mr_warp_compose(const uint16_t (*tab)[kMrStates], uint32_t* wtab, int lane, int S) {
+  for (int x = lane; x < S; x += 32) {
+    uint32_t st = (uint32_t)x, cnt = 0;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const uint32_t e = tab[i][st];
+      cnt += e >> 6;
+      st = e & 63u;
+    }
+    wtab[x] = st | (cnt << 6);
+  }
+}
+
+// Pass 1: each tile's table (kMrStates entries); the pair / forced bits are kept for pass 5.
+template <class K>
+__global__ void __launch_bounds__(kDetectThreads)
+minrun_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+                     int32_t count, int w, uint32_t* __restrict__ tile_tab, uint64_t* __restrict__ thr_L,
+                     uint64_t* __restrict__ thr_F) {
+  __shared__ uint64_t s_L[kDetectThreads], s_F[kDetectThreads];
+  __shared__ uint16_t s_tab[kDetectThreads][kMrStates];
+  __shared__ uint32_t s_wtab[kDetectThreads / 32][kMrStates];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S = w + 2;
+  ThreadRuns<K> tr;
+  tr.load(keys, n, offsets, count, blockIdx.x, tid);
+  const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
+  thr_L[gt] = tr.L;
+  if (offsets != nullptr) thr_F[gt] = tr.F;
+  s_L[tid] = tr.L;
+  s_F[tid] = tr.F;
+  __syncthreads();
+  uint64_t Ln = 0, Fn = 0;
+  if (tid + 1 < kDetectThreads) {
+    Ln = s_L[tid + 1];
+    Fn = s_F[tid + 1];
+  } else if ((int64_t)(blockIdx.x + 1) * kDetectTile < (int64_t)n) {
+    ThreadRuns<K> nx;
+    nx.load(keys, n, offsets, count, blockIdx.x + 1, 0);
+    Ln = nx.L;
+    Fn = nx.F;
+  }
+  uint64_t Lw, Fw;
+  mr_window(tr.L, tr.F, Ln, Fn, tr.p0, n, Lw, Fw);
+  for (int x = 0; x < S; ++x) s_tab[tid][x] = (uint16_t)mr_walk(Lw, Fw, tr.nvalid, w, (uint32_t)x);
+  __syncthreads();
+  mr_warp_compose(&s_tab[warp * 32], s_wtab[warp], lane, S);
+  __syncthreads();
+  if (warp == 0) {
+    for (int x = lane; x < S; x += 32) {
+      uint32_t st = (uint32_t)x, cnt = 0;
+      for (int v = 0; v < kDetectThreads / 32; ++v) {
+        const uint32_t e = s_wtab[v][st];
+        cnt += e >> 6;
+        st = e & 63u;
+      }
+      tile_tab[(size_t)blockIdx.x * kMrStates + x] = st | (cnt << 6);
+    }
+  }
+}
+
+// Pass 2: each group of kMrGroup tiles composed into one table (tables staged in shared memory).
+static __global__ void __launch_bounds__(256)
+minrun_group_kernel(const uint32_t* __restrict__ tile_tab, int32_t ntiles, int w, uint32_t* __restrict__ grp_tab) {
+  __shared__ uint32_t s_t[kMrGroup * kMrStates];
+  const int S = w + 2;
+  const int32_t t0 = blockIdx.x * kMrGroup, nt = min(kMrGroup, ntiles - t0);
+  for (int i = threadIdx.x; i < nt * kMrStates; i += blockDim.x) s_t[i] = tile_tab[(size_t)t0 * kMrStates + i];
+  __syncthreads();
+  if (threadIdx.x < S) {
+    uint32_t st = threadIdx.x, cnt = 0;
+    for (int t = 0; t < nt; ++t) {
+      const uint32_t e = s_t[t * kMrStates + st];
+      cnt += e >> 6;
+      st = e & 63u;
+    }
+    grp_tab[(size_t)blockIdx.x * kMrStates + threadIdx.x] = st | (cnt << 6);
+  }
+}
+
+// Pass 3 (one thread): the groups walked from F(0) at position 0.  grp_pre[g] = entry state of
+// group g | runs before it << 8; hdr->runs = r and S[r] = n.
+static __global__ void minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int32_t n,
+                                         uint64_t* __restrict__ grp_pre, int32_t* __restrict__ S,
+                                         PlanHeader* __restrict__ hdr) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  uint32_t st = 0, cnt = 0;
+  for (int32_t g = 0; g < ngroups; ++g) {
+    grp_pre[g] = (uint64_t)st | ((uint64_t)cnt << 8);
+    const uint32_t e = grp_tab[(size_t)g * kMrStates + st];
+    cnt += e >> 6;
+    st = e & 63u;
+  }
+  hdr->runs = (int32_t)cnt;
+  if (cnt <= (uint32_t)n) S[cnt] = n;
+  else post_status(&hdr->status, nullptr, kDevInternal);  // a run has at least one element
+}
+
+// Pass 4: the entry state and run count of every tile of a group.
+static __global__ void __launch_bounds__(256)
+minrun_tile_kernel(const uint32_t* __restrict__ tile_tab, int32_t ntiles, const uint64_t* __restrict__ grp_pre,
+                   uint64_t* __restrict__ tile_pre) {
+  __shared__ uint32_t s_t[kMrGroup * kMrStates];
+  const int32_t t0 = blockIdx.x * kMrGroup, nt = min(kMrGroup, ntiles - t0);
+  for (int i = threadIdx.x; i < nt * kMrStates; i += blockDim.x) s_t[i] = tile_tab[(size_t)t0 * kMrStates + i];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const uint64_t pre = grp_pre[blockIdx.x];
+    uint32_t st = (uint32_t)(pre & 63u);
+    uint64_t cnt = pre >> 8;
+    for (int t = 0; t < nt; ++t) {
+      tile_pre[t0 + t] = (uint64_t)st | (cnt << 8);
+      const uint32_t e = s_t[t * kMrStates + st];
+      cnt += e >> 6;
+      st = e & 63u;
+    }
+  }
+}
+
+// Pass 5: every thread rebuilds its table from the saved bits, the block finds each thread's
+// entry state and rank, and each thread writes its runs: S[k], flags run_desc[k] (bit 0 first
+// pair strictly descending, bit 1 extended) and segments run_seg[k].
+template <class K>
+__global__ void __launch_bounds__(kDetectThreads)
+minrun_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count, int w,
+                   const uint64_t* __restrict__ tile_pre, const uint64_t* __restrict__ thr_L,
+                   const uint64_t* __restrict__ thr_F, size_t nthreads, int32_t* __restrict__ S,
+                   uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
+  __shared__ uint16_t s_tab[kDetectThreads][kMrStates];
+  __shared__ uint32_t s_wtab[kDetectThreads / 32][kMrStates];
+  __shared__ uint32_t s_entry[kDetectThreads], s_rank[kDetectThreads];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int S_ = w + 2;
+  const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
+  const bool seg = offsets != nullptr;
+  ThreadRuns<K> tr;
+  tr.restore(n, blockIdx.x, tid, thr_L[gt], seg ? thr_F[gt] : (gt == 0 ? 1ull : 0ull));
+  const uint64_t Ln = gt + 1 < nthreads ? thr_L[gt + 1] : 0ull;
+  const uint64_t Fn = (seg && gt + 1 < nthreads) ? thr_F[gt + 1] : 0ull;
+  uint64_t Lw, Fw;
+  mr_window(tr.L, tr.F, Ln, Fn, tr.p0, n, Lw, Fw);
+  for (int x = 0; x < S_; ++x) s_tab[tid][x] = (uint16_t)mr_walk(Lw, Fw, tr.nvalid, w, (uint32_t)x);
+  __syncthreads();
+  mr_warp_compose(&s_tab[warp * 32], s_wtab[warp], lane, S_);
+  __syncthreads();
+  if (lane == 0) {
+    const uint64_t pre = tile_pre[blockIdx.x];
+    uint32_t st = (uint32_t)(pre & 63u), cnt = (uint32_t)(pre >> 8);
+    for (int v = 0; v < warp; ++v) {
+      const uint32_t e = s_wtab[v][st];
+      cnt += e >> 6;
+      st = e & 63u;
+    }
+    for (int i = 0; i < 32; ++i) {
+      const int t = warp * 32 + i;
+      s_entry[t] = st;
+      s_rank[t] = cnt;
+      const uint32_t e = s_tab[t][st];
+      cnt += e >> 6;
+      st = e & 63u;
+    }
+  }
+  __syncwarp();
+  if (tr.nvalid == 0) return;
+  int pos = mr_first(Lw, Fw, w, s_entry[tid]);
+  if (pos < 0) return;
+  uint32_t idx = s_rank[tid];
+  int32_t sg = seg ? segment_of(offsets, count, tr.p0) : 0;
+  while (pos < tr.nvalid) {
+    uint32_t fl;
+    const int nx = mr_next(Lw, Fw, pos, w, fl);
+    const int32_t p = tr.p0 + pos;
+    if (seg && ((tr.F >> pos) & 1ull)) sg = segment_of(offsets, count, p);
+    if (idx < (uint32_t)n) {  // always true when the tables are consistent
+      S[idx] = p;
+      run_desc[idx] = (uint8_t)fl;
+      if (run_seg) run_seg[idx] = sg;
+    }
+    ++idx;
+    if (nx >= 32) break;
+    pos = nx;
+  }
+}
+
+}  // namespace ps

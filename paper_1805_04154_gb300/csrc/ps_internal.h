@@ -37,6 +37,10 @@ struct Ctx {
   uint64_t* thr_L = nullptr;    // per detection thread: pair bits of its 32 positions
   uint64_t* thr_F = nullptr;    // forced-start bits (segmented calls only)
   uint32_t* thr_fn = nullptr;   // its transition function with run counts
+  int min_run = 1;              // minimal run length w (1: greedy runs only)
+  uint32_t* mr_tile_tab = nullptr;  // w > 1: per tile, kMrStates table entries
+  uint32_t* mr_grp_tab = nullptr;   //        per group of kMrGroup tiles
+  uint64_t* mr_grp_pre = nullptr;   //        entry state and runs before each group
   int32_t* tree_sum = nullptr;  // [32 power values][tree_stride tiles]
   int32_t tree_stride = 0;
   int32_t* tree_pre = nullptr;

@@ -5,6 +5,7 @@
 #include <algorithm>
 
 #include "ps_detect.cuh"
+#include "ps_detect_minrun.cuh"
 #include "ps_internal.h"
 #include "ps_fused.cuh"
 #include "ps_level.cuh"
@@ -17,6 +18,7 @@ struct Launch {
   typedef typename K::T T;
 
   static cudaError_t detect(const Ctx& c) {
+    if (c.min_run > 1) return detect_minrun(c);
     detect_reduce_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
         (const T*)c.k[0], c.n, c.offsets, c.count, c.detect_state, c.thr_L, c.thr_F, c.thr_fn);
     detect_scan_kernel<<<1, 1024, 0, c.stream>>>(c.detect_state, c.detect_tiles, c.n, c.detect_state + c.detect_tiles,
@@ -24,6 +26,22 @@ struct Launch {
     detect_emit_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
         c.n, c.offsets, c.count, c.detect_state + c.detect_tiles, c.thr_L, c.thr_F, c.thr_fn, c.S, c.run_desc,
         c.run_seg);
+    return cudaGetLastError();
+  }
+
+  // five launches: tile tables, group tables, the walk over groups, tile entries, emit
+  static cudaError_t detect_minrun(const Ctx& c) {
+    const int32_t tiles = c.detect_tiles, groups = (tiles + kMrGroup - 1) / kMrGroup;
+    const size_t nthreads = (size_t)tiles * kDetectThreads;
+    uint64_t* tile_pre = c.detect_state + c.detect_tiles;
+    minrun_reduce_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>((const T*)c.k[0], c.n, c.offsets, c.count,
+                                                                    c.min_run, c.mr_tile_tab, c.thr_L, c.thr_F);
+    minrun_group_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.min_run, c.mr_grp_tab);
+    minrun_top_kernel<<<1, 32, 0, c.stream>>>(c.mr_grp_tab, groups, c.n, c.mr_grp_pre, c.S, c.hdr);
+    minrun_tile_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.mr_grp_pre, tile_pre);
+    minrun_emit_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>(c.n, c.offsets, c.count, c.min_run, tile_pre,
+                                                                  c.thr_L, c.thr_F, nthreads, c.S, c.run_desc,
+                                                                  c.run_seg);
     return cudaGetLastError();
   }
 

@@ -56,6 +56,7 @@ struct SubElem<K, 4> {
   }
   // positions differ, so two elements never compare equal
   __device__ __forceinline__ static bool before(R a, R b) { return a < b; }
+  __device__ __forceinline__ static bool less(R a, R b) { return a < b; }
   __device__ __forceinline__ static uint32_t key(R x) { return K::unord((uint32_t)(x >> 32)); }
   __device__ __forceinline__ static int32_t pos(R x) { return (int32_t)(uint32_t)x; }
 };
@@ -85,6 +86,10 @@ struct SubElem<K, 8> {
   __device__ __forceinline__ static R make(uint64_t key, int32_t pos) { return R{key, (uint32_t)pos}; }
   // a comes from the left child: it goes first unless its key is greater
   __device__ __forceinline__ static bool before(const R& a, const R& b) { return K::le(a.k, b.k); }
+  // the order of (key, position), for elements of one run
+  __device__ __forceinline__ static bool less(const R& a, const R& b) {
+    return a.k != b.k ? K::le(a.k, b.k) : a.p < b.p;
+  }
   __device__ __forceinline__ static uint64_t key(const R& x) { return x.k; }
   __device__ __forceinline__ static int32_t pos(const R& x) { return (int32_t)x.p; }
 };
@@ -107,6 +112,7 @@ struct SubLayout {
   static constexpr size_t kPay = V ? (size_t)TS * 4 : 0;
   static constexpr size_t kMeta = kNodes > kPay ? kNodes : kPay;
   static_assert(kRuns <= kMeta, "run metadata fits the shared region");
+  static_assert(kRuns + (size_t)TS * 2 <= kMeta, "run metadata and the extended-run sources fit");
   static constexpr size_t kBytes = E::kDataBytes + kMeta;
 };
 
@@ -173,12 +179,13 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
   // 1. run starts and directions; the keys, tagged with their positions
   int16_t* rs = (int16_t*)meta;
   uint8_t* rdsc = (uint8_t*)(rs + RC);
-  bool any_desc = false;
+  bool any_desc = false, any_ext = false;
   for (int32_t k = tid; k <= nr; k += kSubThreads) {
     rs[k] = (int16_t)(S[L + k] - lo);
     if (k < nr) {
       rdsc[k] = run_desc[L + k];
-      any_desc |= rdsc[k] != 0;
+      any_desc |= rdsc[k] == 1;
+      any_ext |= (rdsc[k] & 2) != 0;
     }
   }
   const T* __restrict__ gk = (const T*)buf.k[0];
@@ -190,10 +197,39 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
   for (int t = tid; t < NW * kMaxLevels; t += kSubThreads) (&s_cnt[0][0])[t] = 0;
   if (tid == 0) s_maxrd = -1;
   const int anyd = __syncthreads_or(any_desc);
-
-  // 2. descending runs reversed in place, through registers
+  const int anyx = __syncthreads_or(any_ext);
   const int32_t cs = tid * IPT;
-  if (anyd) {
+
+  // 2a. runs extended to the minimal run length: the element at p goes to its stable rank inside
+  //     its run (the order of key, then position); src[rank] = p records where each output
+  //     position takes its element from
+  int16_t* src = (int16_t*)(meta + Lay::kRuns);
+  if (anyx) {
+    if (cs < m) {
+      int32_t a = 0, b = nr;  // run containing cs
+      while (b - a > 1) {
+        const int32_t mid = (a + b) >> 1;
+        if (rs[mid] <= cs) a = mid;
+        else b = mid;
+      }
+      int32_t k = a;
+      for (int q = 0; q < IPT; ++q) {
+        const int32_t p = cs + q;
+        if (p >= m) break;
+        while (p >= rs[k + 1]) ++k;
+        if (rdsc[k] & 2) {
+          const R x = E::ld(X, sub_slot<E>(p));
+          int32_t rank = rs[k];
+          for (int32_t j = rs[k]; j < rs[k + 1]; ++j) rank += E::less(E::ld(X, sub_slot<E>(j)), x) ? 1 : 0;
+          src[rank] = (int16_t)p;
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // 2b. descending runs reversed and extended runs permuted in place, through registers
+  if (anyd | anyx) {
     R v[IPT];
     uint32_t mv = 0;
     if (cs < m) {
@@ -209,10 +245,10 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
         const int32_t p = cs + q;
         if (p < m) {
           while (p >= rs[k + 1]) ++k;
-          if (rdsc[k]) {
-            const int32_t src = (int32_t)rs[k] + rs[k + 1] - 1 - p;
-            if (src != p) {
-              v[q] = E::ld(X, sub_slot<E>(src));
+          if (rdsc[k] != 0) {
+            const int32_t from = (rdsc[k] & 2) ? (int32_t)src[p] : (int32_t)rs[k] + rs[k + 1] - 1 - p;
+            if (from != p) {
+              v[q] = E::ld(X, sub_slot<E>(from));
               mv |= 1u << q;
             }
           }
@@ -437,7 +473,7 @@ __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restr
   if (i < 0 || i >= runs) return;  // never for a consistent plan (uniform over the CTA)
   const int32_t k = (int32_t)(tile - tile_off[slot]);
   const int32_t s = S[i], e = S[i + 1];
-  const bool desc = run_desc[i] != 0;
+  const bool desc = (run_desc[i] & 1) != 0;  // extended runs (bit 1) are short: never placed here
   const T* __restrict__ k0 = (const T*)buf.k[0];
   const uint32_t* __restrict__ v0 = buf.v[0];
   // all loads of the thread first (independent, coalesced even when reversed), then the stores

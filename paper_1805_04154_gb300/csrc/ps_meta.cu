@@ -444,7 +444,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           atomicAdd(&hdr->small_elems, (unsigned long long)len);
         }
       } else {
-        const bool desc = run_desc[x] != 0;
+        const bool desc = (run_desc[x] & 1) != 0;
+        if (run_desc[x] & 2) post_status(&hdr->status, nullptr, kDevInternal);  // extended runs are short
         uint32_t tiles = 0;
         const bool odd_buf = out_buffer(d, fused != 0) == 1;
         if (odd_buf) tiles = (uint32_t)((len + kMergeTile - 1) / kMergeTile);

@@ -91,6 +91,16 @@ def test_tree_argument_errors_without_gpu(lib):
     assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 1) > lib.ps_workspace_size_tree(0, 1, 1000, 0, 0)
 
 
+def test_minrun_argument_errors_without_gpu(lib):
+    ws = ctypes.c_void_p(256)
+    keys = ctypes.c_void_p(4096)
+    # minimal run length outside [1, 32]: rejected before any CUDA call
+    for w in (0, -3, 33, 1000):
+        assert lib.ps_sort_minrun_ws(0, keys, None, 10, None, 1, w, ws, 1 << 20, None) == 1
+        assert lib.ps_analyze_minrun(0, keys, 10, None, 1, w, ws, 1 << 20, None, None, None, None, None,
+                                     None, None, None, None, None) == 1
+
+
 def test_tuning_table_without_gpu(lib):
     import paper_1805_04154_gb300 as ps
     assert ps.ps_tune_get(0, True) == (12, 2)
