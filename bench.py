@@ -140,22 +140,25 @@ def _cpu_baseline(keys, vals, sample_desc: str):
             "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
 
 
-def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tree: int = 0):
+def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tree: int = 0, min_run: int = 1):
     """Sort throughput of one more workload (resident inputs, fresh copy per step); tree 1 uses
-    peeksort's merge tree (Alg. 1) instead of powersort's."""
+    peeksort's merge tree (Alg. 1) instead of powersort's; min_run > 1 extends short runs to that
+    length first (Sec. 5.1)."""
     import numpy as np
     import torch
     eb = keys.dtype.itemsize + 4
     k0 = torch.from_numpy(keys.view({4: np.int32, 8: np.int64}[keys.dtype.itemsize])).to(dev)
     v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
-    an = ps.ps_analyze(k0, key_type=kt, tree=tree)
+    an = ps.ps_analyze(k0, key_type=kt, tree=tree, min_run=min_run)
     n = keys.size
     ws = torch.empty(ps.ps_workspace_size(kt, True, n, False, tree), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
     copies = [(k0.clone(), v0.clone()) for _ in range(steps + 2)]
 
     def one(i):
-        if tree:
+        if min_run > 1:
+            ps.ps_sort_minrun_ws(copies[i][0], copies[i][1], ws, min_run, key_type=kt, stream=stream)
+        elif tree:
             ps.ps_sort_tree_ws(copies[i][0], copies[i][1], ws, tree, key_type=kt, stream=stream)
         else:
             ps.ps_sort_ws(copies[i][0], copies[i][1], ws, key_type=kt, stream=stream)
@@ -173,7 +176,7 @@ def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tre
     peak, _ = _peaks()
     ideal = an["cost"] * eb * 2 / (peak * 1e9) * 1e3
     del copies, ws, k0, v0
-    return {"workload": name, "n": int(n), "runs": int(an["runs"]), "merge_cost": int(an["cost"]),
+    return {"workload": name, "n": int(n), "min_run": int(min_run), "runs": int(an["runs"]), "merge_cost": int(an["cost"]),
             "ms_per_sort": ms, "gkeys_s": n / (ms / 1e3) / 1e9, "merge_cost_roofline_frac": ideal / ms}
 
 
@@ -596,9 +599,13 @@ def run_gpu(args):
         del hk, hv
         pk, pv = workloads.perm_i32(n, seed=SEED)
         var.append(measure_variant(ps, dev, f"random permutation, n={n} int32 + uint32 (runs ~2.4)", pk, pv, 0))
+        var.append(measure_variant(ps, dev, f"random permutation, n={n}, runs extended to 24 (Sec. 5.1)", pk, pv, 0,
+                                   min_run=24))
         del pk, pv
         rk, rv = workloads.random_runs_i32(10 ** 7, seed=SEED, mean_len=3000)
         var.append(measure_variant(ps, dev, "paper random-runs: n=1e7, geometric run lengths, mean 3000", rk, rv, 0))
+        var.append(measure_variant(ps, dev, "paper random-runs: n=1e7, mean 3000, runs extended to 24 (Sec. 5.1)",
+                                   rk, rv, 0, min_run=24))
         uk, uv = workloads.pareto_u64(n, seed=SEED, alpha=1.2, distinct=1000, max_len=n // 10)
         var.append(measure_variant(ps, dev, f"uint64 keys from 1000 values, Pareto(1.2) runs, n={n} + uint32", uk, uv, 2))
         del uk, uv
@@ -638,9 +645,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--batched-segments", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=300)
-    ap.add_argument("--once", choices=["runs", "perm"], default=None,
-                    help="profiling driver: exactly one ps_sort_ws of the headline (runs) or permutation "
-                         "workload at --n, no warm-up, no JSON line")
+    ap.add_argument("--once", choices=["runs", "perm", "runs_minrun24", "perm_minrun24"], default=None,
+                    help="profiling driver: exactly one sort of the headline (runs) or permutation workload "
+                         "(*_minrun24: runs extended to 24) at --n, no warm-up, no JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.once:
@@ -660,12 +667,15 @@ def run_once(args):
     import paper_1805_04154_gb300 as ps
     ps.load()
     n = args.n
-    keys, vals = _gen(n, SEED) if args.once == "runs" else workloads.perm_i32(n, seed=SEED)
+    keys, vals = _gen(n, SEED) if args.once.startswith("runs") else workloads.perm_i32(n, seed=SEED)
     dk = torch.from_numpy(keys).cuda()
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
     ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n), dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
-    ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
+    if args.once.endswith("_minrun24"):
+        ps.ps_sort_minrun_ws(dk, dv, ws, 24, key_type=ps.PS_KEY_I32)
+    else:
+        ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
     torch.cuda.synchronize()
     ok = ps.ps_stream_status() == 0 and bool((dk[1:] >= dk[:-1]).all().item())
     print(f"once {args.once} n={n} sorted={ok}")

@@ -94,6 +94,81 @@ __device__ __forceinline__ uint32_t mr_walk(uint64_t Lw, uint64_t Fw, int nvalid
   return ex | (cnt << 6);
 }
 
+// bit i = OR of the bits [i, i + width) of b
+__device__ __forceinline__ uint64_t mr_smear(uint64_t b, int width) {
+  if (width <= 0) return 0;
+  uint64_t r = b;
+  for (int c = 1; c < width;) {
+    const int sh = min(c, width - c);
+    r |= r >> sh;
+    c += sh;
+  }
+  return r;
+}
+
+// A full window (32 positions owned, the next 32 visible).  A start q is "regular" when its run
+// is extended to exactly q + w: no forced start in (q, q + w) and a break of its direction in
+// [q + 2, q + w).  Bit q of the result (q < 32) marks the other starts.  From a regular start the
+// chain steps by w, so a walk jumps over all regular starts of the progression pos, pos + w, ...
+// at once.
+__device__ __forceinline__ uint32_t mr_irregular(uint64_t Lw, uint64_t Fw, int w) {
+  const uint64_t Ba = ~Lw | Fw, Bd = Lw | Fw;        // positions that end an ascending / descending run
+  const uint64_t nfa = ~(Fw >> 1);                   // q + 1 is not forced
+  const uint64_t longA = (Lw >> 1) & nfa & ~(mr_smear(Ba, w - 2) >> 2);
+  const uint64_t longD = ~(Lw >> 1) & nfa & ~(mr_smear(Bd, w - 2) >> 2);
+  return (uint32_t)(longA | longD | (mr_smear(Fw, w - 1) >> 1));
+}
+
+// Table entry of a full window for a chain whose first start is pos; prog = bits 0, w, 2w, ... < 32.
+__device__ __forceinline__ uint32_t mr_walk_fast(uint64_t Lw, uint64_t Fw, uint32_t X, uint32_t prog, int w, int pos) {
+  uint32_t cnt = 0;
+  for (;;) {
+    const uint32_t pr = prog << pos;
+    const uint32_t hit = pr & X;
+    if (!hit) {
+      cnt += (uint32_t)__popc(pr);
+      const int last = 31 - __clz(pr);
+      return (uint32_t)(last + w - 32) | (cnt << 6);
+    }
+    const int h = __ffs(hit) - 1;
+    cnt += (uint32_t)__popc(pr & ((1u << h) - 1u)) + 1u;
+    uint32_t fl;
+    const int nx = mr_next(Lw, Fw, h, w, fl);
+    if (nx >= 32) return mr_exit(nx, fl, w) | (cnt << 6);
+    pos = nx;
+  }
+}
+
+// The thread's whole table (entries for states 0 .. w + 1) into row[].
+__device__ __forceinline__ void mr_table(uint64_t Lw, uint64_t Fw, int nvalid, int w, uint16_t* row) {
+  if (nvalid < 32) {
+    for (int x = 0; x < w + 2; ++x) row[x] = (uint16_t)mr_walk(Lw, Fw, nvalid, w, (uint32_t)x);
+    return;
+  }
+  const uint64_t Ba = ~Lw | Fw, Bd = Lw | Fw;
+  row[w] = (uint16_t)mr_walk(Lw, Fw, nvalid, w, (uint32_t)w);
+  row[w + 1] = (uint16_t)mr_walk(Lw, Fw, nvalid, w, (uint32_t)w + 1);
+  if ((Ba >> 1) == 0 || (Bd >> 1) == 0) {
+    // one ascending (descending) stretch covers positions 1..63: a run started at any q < 32 is
+    // still open after the window
+    const uint16_t open = (uint16_t)(((Ba >> 1) == 0 ? w : w + 1) | (1 << 6));
+    for (int k = 0; k < w; ++k) row[k] = open;
+    return;
+  }
+  const uint32_t X = mr_irregular(Lw, Fw, w);
+  uint32_t prog = 0;
+  for (int q = 0; q < 32; q += w) prog |= 1u << q;
+  const uint32_t F32 = (uint32_t)Fw;
+  const int f = F32 ? __ffs(F32) - 1 : 32;  // entry F(k) starts at min(k, f)
+  for (int k = 0; k < w; ++k) {
+    if (k > f) {
+      row[k] = row[f];
+    } else {
+      row[k] = (uint16_t)mr_walk_fast(Lw, Fw, X, prog, w, k);
+    }
+  }
+}
+
 // The window of one detection thread: its own pair / forced bits (positions 0..32) and those
 // of the next thread (positions 32..64); positions at or past n are marked forced (a stop).
 __device__ __forceinline__ void mr_window(uint64_t L, uint64_t F, uint64_t Ln, uint64_t Fn, int32_t p0, int32_t n,
@@ -150,7 +225,7 @@ minrun_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const in
   }
   uint64_t Lw, Fw;
   mr_window(tr.L, tr.F, Ln, Fn, tr.p0, n, Lw, Fw);
-  for (int x = 0; x < S; ++x) s_tab[tid][x] = (uint16_t)mr_walk(Lw, Fw, tr.nvalid, w, (uint32_t)x);
+  mr_table(Lw, Fw, tr.nvalid, w, s_tab[tid]);
   __syncthreads();
   mr_warp_compose(&s_tab[warp * 32], s_wtab[warp], lane, S);
   __syncthreads();
@@ -247,7 +322,7 @@ minrun_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count
   const uint64_t Fn = (seg && gt + 1 < nthreads) ? thr_F[gt + 1] : 0ull;
   uint64_t Lw, Fw;
   mr_window(tr.L, tr.F, Ln, Fn, tr.p0, n, Lw, Fw);
-  for (int x = 0; x < S_; ++x) s_tab[tid][x] = (uint16_t)mr_walk(Lw, Fw, tr.nvalid, w, (uint32_t)x);
+  mr_table(Lw, Fw, tr.nvalid, w, s_tab[tid]);
   __syncthreads();
   mr_warp_compose(&s_tab[warp * 32], s_wtab[warp], lane, S_);
   __syncthreads();
