@@ -19,12 +19,6 @@ constexpr int kDetectThreads = 256;
 constexpr int kDetectItems = 32;
 constexpr int kDetectTile = kDetectThreads * kDetectItems;  // 8192
 
-// Stage 1 with a minimal run length w (Sec. 5.1): w <= kMinRunMax; transfer functions are
-// tables of kMrStates entries; the tile scan composes groups of kMrGroup tiles.
-constexpr int kMinRunMax = 32;
-constexpr int kMrStates = kMinRunMax + 2;
-constexpr int kMrGroup = 256;
-
 // Stage 3 (nearest-smaller-value tree): 256 threads x 32 consecutive boundaries per tile.
 constexpr int kTreeThreads = 256;
 constexpr int kTreeChunk = 32;

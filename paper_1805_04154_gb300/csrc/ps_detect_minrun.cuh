@@ -26,6 +26,7 @@
 
 #include "ps_common.cuh"
 #include "ps_detect.cuh"
+#include "ps_internal.h"
 
 namespace ps {
 

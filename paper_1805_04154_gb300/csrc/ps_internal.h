@@ -10,6 +10,12 @@
 
 namespace ps {
 
+// Stage 1 with a minimal run length w (Sec. 5.1): w <= kMinRunMax; transfer functions are
+// tables of kMrStates entries; the tile scan composes groups of kMrGroup tiles.
+constexpr int kMinRunMax = 32;
+constexpr int kMrStates = kMinRunMax + 2;
+constexpr int kMrGroup = 256;
+
 struct Ctx {
   cudaStream_t stream = nullptr;
   int kt = 0;            // key type (powersort.h ps_key_type)
