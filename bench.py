@@ -489,7 +489,10 @@ def run_gpu(args):
                 tr = json.load(f)
             csrc = os.path.join(ROOT, "paper_1805_04154_gb300", "csrc")
             src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in tr.get("sources", []))
-            if src and tr.get("source_sha256") == hashlib.sha256(src).hexdigest() and mt["launches"]:
+            cfg = ps.ps_tune_get(ps.PS_KEY_I32, True)
+            same_cfg = list(tr.get("config", [])) == [int(cfg[0]), int(cfg[1])]
+            if (src and same_cfg and tr.get("source_sha256") == hashlib.sha256(src).hexdigest()
+                    and mt["launches"]):
                 elems_per_launch = mt["bytes"] / (2 * eb) / mt["launches"]
                 traffic = tr["dram_bytes_per_output_elem"] * elems_per_launch
         except Exception:
@@ -672,13 +675,18 @@ def run_once(args):
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
     ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n), dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
+    ps.ps_profile_enable(True)
     if args.once.endswith("_minrun24"):
         ps.ps_sort_minrun_ws(dk, dv, ws, 24, key_type=ps.PS_KEY_I32)
     else:
         ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
     torch.cuda.synchronize()
+    prof = ps.ps_profile_read()
+    ps.ps_profile_enable(False)
     ok = ps.ps_stream_status() == 0 and bool((dk[1:] >= dk[:-1]).all().item())
-    print(f"once {args.once} n={n} sorted={ok}")
+    lp = prof["level_pass"]
+    print(f"once {args.once} n={n} sorted={ok} level_pass_launches={lp['launches']} "
+          f"level_pass_outputs={lp['bytes'] // 16} config={ps.ps_tune_get(ps.PS_KEY_I32, True)}")
     return 0 if ok else 1
 
 

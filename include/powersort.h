@@ -161,7 +161,7 @@ ps_status ps_selftest_wait_timeout(uint32_t polls, void* stream);
  * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
  * shared-memory buffers; the library carries the configurations (12, 2), (12, 3), (12, 4),
  * (8, 2), (8, 3) and (16, 2).  One configuration per key type and payload choice is used by every
- * later sort on this process (default (12, 2)). */
+ * later sort on this process (default (8, 2)). */
 typedef struct {
   int items_per_thread;    /* the chosen configuration */
   int stages;

@@ -202,8 +202,10 @@ struct AnalyzeOut {
 };
 
 // Level-pass configuration (items per consumer thread, ring stages), per key type and payload
-// choice: 12 items and 2 stages unless PS_PASS_STAGES picks another compiled ring depth for 12
+// choice: 8 items and 2 stages unless PS_PASS_STAGES picks another compiled ring depth for 8
 // items, ps_tune_set or ps_autotune choose otherwise.  Packed as pass_variant(ipt, stages).
+constexpr int kDefaultPassIpt = 8;  // outputs per consumer thread of the default level pass
+
 bool known_variant(int ipt, int stages) {
   for (int i = 0; i < kPassVariants; ++i)
     if (kPassVariantIpt[i] == ipt && kPassVariantStages[i] == stages) return true;
@@ -215,7 +217,7 @@ int default_variant() {
   if (v < 0) {
     const char* e = std::getenv("PS_PASS_STAGES");
     const int x = e ? std::atoi(e) : 0;
-    v = known_variant(kMergeItems, x) ? pass_variant(kMergeItems, x) : pass_variant(kMergeItems, 2);
+    v = known_variant(kDefaultPassIpt, x) ? pass_variant(kDefaultPassIpt, x) : pass_variant(kDefaultPassIpt, 2);
   }
   return v;
 }

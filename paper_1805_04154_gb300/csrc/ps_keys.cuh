@@ -86,26 +86,41 @@ struct Launch {
     return c.has_vals ? small_v<true>(c, ntasks) : small_v<false>(c, ntasks);
   }
 
+  // resident CTAs per SM of a 256-thread kernel without dynamic shared memory
+  template <class Kern>
+  static int resident(Kern kern) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kern, 256, 0) != cudaSuccess || b < 1) b = 1;
+    return b;
+  }
+
   static cudaError_t place(const Ctx& c, uint32_t nitems, uint32_t ntiles) {
     if (ntiles == 0) return cudaSuccess;
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     const uint32_t cap = (uint32_t)c.level_cap;
     const int fu = c.fused ? 1 : 0;
+    static int occ_v = 0, occ_k = 0;
+    if (occ_v == 0) {
+      occ_v = resident(leaf_place_kernel<K, true>);
+      occ_k = resident(leaf_place_kernel<K, false>);
+    }
+    const uint32_t full = (uint32_t)sm_count() * (uint32_t)(c.has_vals ? occ_v : occ_k);
     if (ntiles == kCountOnDevice) {
-      const uint32_t grid = (uint32_t)sm_count() * 8;
       if (c.has_vals)
-        leaf_place_persistent_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+        leaf_place_persistent_kernel<K, true><<<full, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
                                                                           c.leaf_tile_off, cap, fu, c.hdr);
       else
-        leaf_place_persistent_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth,
+        leaf_place_persistent_kernel<K, false><<<full, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth,
                                                                            c.leaf_items, c.leaf_tile_off, cap, fu,
                                                                            c.hdr);
-    } else if (c.has_vals) {
-      leaf_place_kernel<K, true><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                               c.leaf_tile_off, nitems, fu, c.hdr);
     } else {
-      leaf_place_kernel<K, false><<<ntiles, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                                c.leaf_tile_off, nitems, fu, c.hdr);
+      const uint32_t grid = std::min(ntiles, full);
+      if (c.has_vals)
+        leaf_place_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                               c.leaf_tile_off, nitems, ntiles, fu, c.hdr);
+      else
+        leaf_place_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
+                                                                c.leaf_tile_off, nitems, ntiles, fu, c.hdr);
     }
     return cudaGetLastError();
   }
@@ -123,7 +138,7 @@ struct Launch {
       cudaGetDevice(&dev);
       cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, level_pass_kernel<K, V, NS, IPT>,
-                                                        kPassThreads, bytes);
+                                                        kLevelThreads, bytes);
       if (e != cudaSuccess) return e;
       if (blocks_per_sm < 1) blocks_per_sm = 1;
     }
@@ -132,7 +147,7 @@ struct Launch {
     const bool on_dev = ntiles == kCountOnDevice;
     const uint32_t grid = on_dev ? (uint32_t)(sms * blocks_per_sm)
                                  : (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
-    level_pass_kernel<K, V, NS, IPT><<<grid, kPassThreads, bytes, c.stream>>>(
+    level_pass_kernel<K, V, NS, IPT><<<grid, kLevelThreads, bytes, c.stream>>>(
         (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.level_tile_off + off, nitems,
         ntiles, on_dev ? &c.hdr->level_ctr[depth] : nullptr, (uint32_t)c.level_cap, c.hdr, c.lib_status);
     return cudaGetLastError();

@@ -14,18 +14,30 @@ namespace ps {
 // tile size (IPT outputs per consumer thread x 256 threads) inside it.  Persistent and warp-specialized:
 //  * CTA b owns the contiguous tile range [b*T/G, (b+1)*T/G) of the pass (T tiles, G CTAs), so
 //    the co-rank at the end of one tile is the co-rank at the start of the next;
-//  * warp 8 (producer) walks the CTA's tiles: it finds each tile's end co-rank with a 32-way
-//    warp search inside the window the start co-rank allows (at most one tile wide; its
-//    probes touch the lines the tile's copy then reads), waits for a free stage, and issues the
-//    tile's four bulk copies (left/right keys and payloads, 16-byte aligned chunks) on that
-//    stage's "full" mbarrier;
+//  * warp 9 (searcher) walks the CTA's tiles in batches: it finds each tile's end co-rank with
+//    an 8-way search in global memory inside the window the last known co-rank allows, and
+//    publishes the searched tiles in a shared-memory queue of kQueue entries (one mbarrier pair
+//    per entry), running ahead of the copies so that the searches' global-memory latency
+//    overlaps the merges;
+//  * warp 8 (issuer, one thread) takes the next searched tile, waits for a free stage, and
+//    issues the tile's four bulk copies (left/right keys and payloads, 16-byte aligned chunks)
+//    on that stage's "full" mbarrier;
 //  * warps 0-7 (consumers) wait for a full stage, merge its IPT outputs per thread
 //    (co-rank inside shared memory, then a serial stable merge), write them with 128-bit
 //    stores, and release the stage on its "empty" mbarrier.
 // A ring of NS stages: the copies of the next NS-1 tiles overlap the merge of the current one.
 // All waits are bounded; a timeout posts kDevTimeout and the CTA drains its copies and exits.
 // ---------------------------------------------------------------------------------------
-constexpr int kPassThreads = kMergeThreads + 32;  // 8 consumer warps + 1 producer warp
+constexpr int kPassThreads = kMergeThreads + 32;   // 8 consumer warps + 1 producer warp (fused passes)
+constexpr int kLevelThreads = kMergeThreads + 64;  // 8 consumer warps + issuer + searcher
+constexpr int kQueue = 8;                          // searched tiles the searcher may run ahead
+constexpr int kSearchBatch = 4;                    // tiles searched together (8 lanes each)
+
+// A searched tile: its node (lo, mid, hi, boundary), outputs [g0, g1), left elements [i0, i1).
+struct QueuedTile {
+  int4 nd;
+  int32_t g0, g1, i0, i1;
+};
 
 struct StageDesc {
   int32_t g0, g1, i0, i1;   // outputs [g0, g1); left elements [i0, i1) of the node
@@ -47,7 +59,9 @@ struct PassLayout {
   static constexpr size_t kStageBytes = kKeyBytes + kValBytes;
   static constexpr size_t kBarOff = 0;  // full[NS], empty[NS]
   static constexpr size_t kDescOff = (2 * NS * 8 + 63) & ~(size_t)63;  // StageDesc[NS]
-  static constexpr size_t kFlagOff = kDescOff + NS * sizeof(StageDesc);
+  static constexpr size_t kQBarOff = kDescOff + NS * sizeof(StageDesc);  // qfull[kQueue], qempty[kQueue]
+  static constexpr size_t kQueueOff = (kQBarOff + 2 * kQueue * 8 + 63) & ~(size_t)63;  // QueuedTile[kQueue]
+  static constexpr size_t kFlagOff = kQueueOff + kQueue * sizeof(QueuedTile);
   static constexpr size_t kStageOff = (kFlagOff + 16 + 127) & ~(size_t)127;
   static constexpr size_t kBytes = kStageOff + NS * kStageBytes;
 };
@@ -108,7 +122,7 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
 __host__ __device__ constexpr int pass_min_blocks(int ipt) { return ipt <= 12 ? 4 : 3; }
 
 template <class K, bool V, int NS, int IPT>
-__global__ void __launch_bounds__(kPassThreads, pass_min_blocks(IPT))
+__global__ void __launch_bounds__(kLevelThreads, pass_min_blocks(IPT))
 level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __restrict__ srcv,
                   typename K::T* __restrict__ dstk, uint32_t* __restrict__ dstv,
                   const int4* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
@@ -136,18 +150,25 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
   const uint32_t t_begin = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
   const uint32_t t_end = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
   if (t_begin >= t_end) return;  // no tile for this CTA (uniform over the CTA)
+  uint64_t* qfull = (uint64_t*)(smem + Lay::kQBarOff);
+  uint64_t* qempty = qfull + kQueue;
+  QueuedTile* queue = (QueuedTile*)(smem + Lay::kQueueOff);
   if (threadIdx.x == 0) {
     for (int s = 0; s < kPassStages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], kMergeThreads / 32);
+    }
+    for (int q = 0; q < kQueue; ++q) {
+      mbar_init(&qfull[q], 1);
+      mbar_init(&qempty[q], 1);
     }
     *abort_flag = 0;
     fence_mbar_init();
   }
   __syncthreads();
 
-  if (warp == kMergeThreads / 32) {
-    // ------------------------------ producer ------------------------------
+  if (warp == kMergeThreads / 32 + 1) {
+    // ------------------------------ searcher ------------------------------
     int32_t slot = 0;
     if (lane == 0) slot = slot_of_tile(tile_off, nitems, t_begin);
     slot = __shfl_sync(0xffffffffu, slot, 0);
@@ -162,14 +183,13 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       const int32_t diag = g0 - nd.x;
       i0 = warp_corank<K>(A, B, diag, max(0, diag - lb), min(diag, la));
     }
-    // Tiles go out in batches of kSearchBatch: lane group m (8 lanes) finds the end co-rank of
-    // the batch's tile m with an 8-way search, all groups at once.  Each window is anchored at
-    // the last co-rank known in the same node (the batch start, or 0 at a node's first tile),
-    // so it is at most kSearchBatch tiles wide.
-    constexpr int kSearchBatch = 4;
+    // Batches of kSearchBatch tiles: lane group m (8 lanes) finds the end co-rank of the batch's
+    // tile m with an 8-way search, all groups at once.  Each window is anchored at the last
+    // co-rank known in the same node (the batch start, or 0 at a node's first tile), so it is at
+    // most kSearchBatch tiles wide.
     const int grp = lane >> 3, gl = lane & 7;
     const uint32_t gmask = 0xFFu << (grp * 8);
-    uint32_t issued = 0;
+    uint32_t published = 0;
     bool ok = true;
     uint32_t t = t_begin;
     while (t < t_end && ok) {
@@ -245,63 +265,36 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       int32_t m_i1[kSearchBatch];
 #pragma unroll
       for (int m = 0; m < kSearchBatch; ++m) m_i1[m] = __shfl_sync(0xffffffffu, res, m * 8);
-      // issue the batch in order
+      // wait for the batch's queue slots, publish the searched tiles
 #pragma unroll
       for (int m = 0; m < kSearchBatch; ++m) {
         if (m < nb && ok) {
-          const int4 cnd = m_nd[m];
-          const int32_t cla = cnd.y - cnd.x;
-          const int32_t tg0 = m_g0[m], tg1 = m_g1[m];
-          const int32_t ti0 = m_new[m] ? 0 : (m == 0 ? i0 : m_i1[m - 1]);
-          const int32_t ti1 = (tg1 < cnd.z) ? m_i1[m] : cla;
-          const int s = (int)(issued % kPassStages);
-          const uint32_t use = issued / kPassStages;
-          if (!__all_sync(0xffffffffu, bounded_wait(&empty[s], (use & 1u) ^ 1u))) {
-            ok = false;
-          } else {
-            if (lane == 0) {
-              const int32_t a0 = cnd.x + ti0, a1 = cnd.x + ti1;
-              const int32_t b0 = cnd.y + (tg0 - cnd.x - ti0), b1 = cnd.y + (tg1 - cnd.x - ti1);
-              // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only
-              // need natural alignment; a chunk may start up to 15 bytes before a range and end up
-              // to 15 bytes after it, always inside 16-byte blocks holding range elements)
-              int32_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
-              chunk16(srck, a0, a1, ka0, ka1);
-              chunk16(srck, b0, b1, kb0, kb1);
-              chunk16(srcv, a0, a1, va0, va1);
-              chunk16(srcv, b0, b1, vb0, vb1);
-              StageDesc d;
-              d.g0 = tg0;
-              d.g1 = tg1;
-              d.i0 = ti0;
-              d.i1 = ti1;
-              d.lo = cnd.x;
-              d.mid = cnd.y;
-              d.la = cla;
-              d.lb = cnd.z - cnd.y;
-              d.aoff = a0 - ka0;
-              d.boff = (ka1 - ka0) + (b0 - kb0);
-              d.vaoff = a0 - va0;
-              d.vboff = (va1 - va0) + (b0 - vb0);
-              sdesc[s] = d;
-              uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
-              T* sk = (T*)stage;
-              uint32_t* sv = (uint32_t*)(stage + Lay::kKeyBytes);
-              const uint32_t kba = (uint32_t)(ka1 - ka0) * sizeof(T), kbb = (uint32_t)(kb1 - kb0) * sizeof(T);
-              const uint32_t vba = V ? (uint32_t)(va1 - va0) * 4u : 0u, vbb = V ? (uint32_t)(vb1 - vb0) * 4u : 0u;
-              mbar_arrive_expect_tx(&full[s], kba + kbb + vba + vbb);
-              if (kba) bulk_g2s(sk, srck + ka0, kba, &full[s]);
-              if (kbb) bulk_g2s(sk + (ka1 - ka0), srck + kb0, kbb, &full[s]);
-              if (V) {
-                if (vba) bulk_g2s(sv, srcv + va0, vba, &full[s]);
-                if (vbb) bulk_g2s(sv + (va1 - va0), srcv + vb0, vbb, &full[s]);
-              }
+          const uint32_t idx = published + m;
+          int good = 1;
+          if (lane == 0) {
+            good = 0;
+            for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+              if (mbar_try_wait(&qempty[idx % kQueue], ((idx / kQueue) & 1u) ^ 1u)) { good = 1; break; }
+              if (*abort_flag) break;
             }
-            __syncwarp();
-            ++issued;
           }
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) { ok = false; break; }
+          if (lane == 0) {
+            const int4 cnd = m_nd[m];
+            QueuedTile q;
+            q.nd = cnd;
+            q.g0 = m_g0[m];
+            q.g1 = m_g1[m];
+            q.i0 = m_new[m] ? 0 : (m == 0 ? i0 : m_i1[m - 1]);
+            q.i1 = (m_g1[m] < cnd.z) ? m_i1[m] : (cnd.y - cnd.x);
+            queue[idx % kQueue] = q;
+            mbar_arrive(&qfull[idx % kQueue]);
+          }
+          __syncwarp();
         }
       }
+      published += nb;
       // carry the state to the next batch: next tile starts where the batch's last tile ended
       slot = m_slot[0];
       nd = m_nd[0];
@@ -318,16 +311,77 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       if (nb == 1) i0 = (m_g1[0] < m_nd[0].z) ? m_i1[0] : (m_nd[0].y - m_nd[0].x);
       t += nb;
     }
+    if (!ok && lane == 0) {
+      if (!*abort_flag) post_status(&hdr->status, lib_status, kDevTimeout);
+      *abort_flag = 1;
+    }
+  } else if (warp == kMergeThreads / 32) {
+    // ------------------------------ issuer ------------------------------
+    if (lane != 0) return;  // one thread issues; the others have nothing to do
+    const uint32_t total = t_end - t_begin;
+    uint32_t issued = 0;
+    bool ok = true;
+    for (; issued < total; ++issued) {
+      const uint32_t q = issued % kQueue;
+      bool good = false;
+      for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+        if (mbar_try_wait(&qfull[q], (issued / kQueue) & 1u)) { good = true; break; }
+        if (*abort_flag) break;
+      }
+      if (!good) { ok = false; break; }
+      const QueuedTile qt = queue[q];
+      mbar_arrive(&qempty[q]);
+      const int s = (int)(issued % kPassStages);
+      const uint32_t use = issued / kPassStages;
+      if (!bounded_wait(&empty[s], (use & 1u) ^ 1u)) { ok = false; break; }
+      const int4 cnd = qt.nd;
+      const int32_t cla = cnd.y - cnd.x;
+      const int32_t tg0 = qt.g0, tg1 = qt.g1, ti0 = qt.i0, ti1 = qt.i1;
+      const int32_t a0 = cnd.x + ti0, a1 = cnd.x + ti1;
+      const int32_t b0 = cnd.y + (tg0 - cnd.x - ti0), b1 = cnd.y + (tg1 - cnd.x - ti1);
+      // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only need
+      // natural alignment; a chunk may start up to 15 bytes before a range and end up to 15
+      // bytes after it, always inside 16-byte blocks holding range elements)
+      int32_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
+      chunk16(srck, a0, a1, ka0, ka1);
+      chunk16(srck, b0, b1, kb0, kb1);
+      chunk16(srcv, a0, a1, va0, va1);
+      chunk16(srcv, b0, b1, vb0, vb1);
+      StageDesc d;
+      d.g0 = tg0;
+      d.g1 = tg1;
+      d.i0 = ti0;
+      d.i1 = ti1;
+      d.lo = cnd.x;
+      d.mid = cnd.y;
+      d.la = cla;
+      d.lb = cnd.z - cnd.y;
+      d.aoff = a0 - ka0;
+      d.boff = (ka1 - ka0) + (b0 - kb0);
+      d.vaoff = a0 - va0;
+      d.vboff = (va1 - va0) + (b0 - vb0);
+      sdesc[s] = d;
+      uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
+      T* sk = (T*)stage;
+      uint32_t* sv = (uint32_t*)(stage + Lay::kKeyBytes);
+      const uint32_t kba = (uint32_t)(ka1 - ka0) * sizeof(T), kbb = (uint32_t)(kb1 - kb0) * sizeof(T);
+      const uint32_t vba = V ? (uint32_t)(va1 - va0) * 4u : 0u, vbb = V ? (uint32_t)(vb1 - vb0) * 4u : 0u;
+      mbar_arrive_expect_tx(&full[s], kba + kbb + vba + vbb);
+      if (kba) bulk_g2s(sk, srck + ka0, kba, &full[s]);
+      if (kbb) bulk_g2s(sk + (ka1 - ka0), srck + kb0, kbb, &full[s]);
+      if (V) {
+        if (vba) bulk_g2s(sv, srcv + va0, vba, &full[s]);
+        if (vbb) bulk_g2s(sv + (va1 - va0), srcv + vb0, vbb, &full[s]);
+      }
+    }
     if (!ok) {
-      if (lane == 0) post_status(&hdr->status, lib_status, kDevTimeout);
+      post_status(&hdr->status, lib_status, kDevTimeout);
       *abort_flag = 1;
     }
     // drain: every copy issued into a stage must have landed before the CTA exits
-    if (lane == 0) {
-      for (uint32_t q = (issued > kPassStages ? issued - kPassStages : 0); q < issued; ++q) {
-        const int s = (int)(q % kPassStages);
-        bounded_wait(&full[s], (q / kPassStages) & 1u);
-      }
+    for (uint32_t q = (issued > kPassStages ? issued - kPassStages : 0); q < issued; ++q) {
+      const int s = (int)(q % kPassStages);
+      bounded_wait(&full[s], (q / kPassStages) & 1u);
     }
   } else {
     // ------------------------------ consumers ------------------------------

@@ -455,23 +455,15 @@ subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t
 
 // ---------------------------------------------------------------------------------------
 // Large leaves whose depth maps to the scratch buffer -> copied there (reversed if
-// descending); the others, if descending -> reversed in place.  One CTA per kMergeTile outputs
-// (or pairs).
+// descending); the others, if descending -> reversed in place.  Work is cut into tiles of
+// kMergeTile outputs (or pairs); a CTA owns a contiguous range of tiles, finds the leaf of its
+// first tile once and walks the leaf list from there.
 // ---------------------------------------------------------------------------------------
 template <class K, bool V>
-__device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
-                                                const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                                                const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t tile,
-                                                int fused, int32_t runs) {
+__device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+                                               const uint8_t* __restrict__ ldepth, int32_t i, uint32_t k, int fused) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
-  __shared__ int32_t s_slot;
-  if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, tile);
-  __syncthreads();
-  const int32_t slot = s_slot;
-  const int32_t i = items[slot];
-  if (i < 0 || i >= runs) return;  // never for a consistent plan (uniform over the CTA)
-  const int32_t k = (int32_t)(tile - tile_off[slot]);
   const int32_t s = S[i], e = S[i + 1];
   const bool desc = (run_desc[i] & 1) != 0;  // extended runs (bit 1) are short: never placed here
   const T* __restrict__ k0 = (const T*)buf.k[0];
@@ -482,7 +474,7 @@ __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restr
   if (out_buffer(ldepth[i], fused != 0) == 1) {
     T* __restrict__ k1 = (T*)buf.k[1];
     uint32_t* __restrict__ v1 = buf.v[1];
-    const int32_t q0 = s + k * kMergeTile + threadIdx.x, q1 = min(e, s + (k + 1) * kMergeTile);
+    const int32_t q0 = s + (int32_t)k * kMergeTile + threadIdx.x, q1 = min(e, s + ((int32_t)k + 1) * kMergeTile);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int32_t q = q0 + u * 256;
@@ -504,7 +496,7 @@ __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restr
     T* kk = (T*)buf.k[0];
     uint32_t* vv = buf.v[0];
     const int32_t half = (e - s) / 2;
-    const int32_t p0 = s + k * kMergeTile + threadIdx.x, p1 = min(s + half, s + (k + 1) * kMergeTile);
+    const int32_t p0 = s + (int32_t)k * kMergeTile + threadIdx.x, p1 = min(s + half, s + ((int32_t)k + 1) * kMergeTile);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int32_t p = p0 + u * 256;
@@ -534,17 +526,40 @@ __device__ __forceinline__ void leaf_place_tile(Bufs buf, const int32_t* __restr
   }
 }
 
-// One CTA per tile (the count known on the host).
+// Tiles [t_begin, t_end) of the leaf list (items[slot] = leaf, its first tile tile_off[slot]).
+// Tiles touch disjoint elements, so the threads need no barrier between tiles.
+template <class K, bool V>
+__device__ __forceinline__ void leaf_place_range(Bufs buf, const int32_t* __restrict__ S,
+                                                 const uint8_t* __restrict__ run_desc,
+                                                 const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
+                                                 const uint32_t* __restrict__ tile_off, uint32_t nitems,
+                                                 uint32_t t_begin, uint32_t t_end, int fused, int32_t runs) {
+  __shared__ int32_t s_slot;
+  if (t_begin >= t_end || nitems == 0) return;  // uniform over the CTA
+  if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, t_begin);
+  __syncthreads();
+  int32_t slot = s_slot;
+  for (uint32_t tile = t_begin; tile < t_end; ++tile) {
+    while (slot + 1 < (int32_t)nitems && tile_off[slot + 1] <= tile) ++slot;
+    const int32_t i = items[slot];
+    if (i < 0 || i >= runs) return;  // never for a consistent plan (uniform over the CTA)
+    leaf_place_one<K, V>(buf, S, run_desc, ldepth, i, tile - tile_off[slot], fused);
+  }
+}
+
+// Grid over the counts known on the host: CTA b owns tiles [b*T/G, (b+1)*T/G).
 template <class K, bool V>
 __global__ void __launch_bounds__(256)
 leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                   const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                  const uint32_t* __restrict__ tile_off, uint32_t nitems, int fused,
+                  const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t ntiles, int fused,
                   const PlanHeader* __restrict__ hdr) {
-  leaf_place_tile<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, blockIdx.x, fused, hdr->runs);
+  const uint32_t t0 = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, fused, hdr->runs);
 }
 
-// A persistent grid over the counts the plan left on the device (no host round trip).
+// The same over the counts the plan left on the device (no host round trip).
 template <class K, bool V>
 __global__ void __launch_bounds__(256)
 leaf_place_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
@@ -555,12 +570,9 @@ leaf_place_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint
   const unsigned long long v = hdr->leaf_ctr;
   const uint32_t nitems = min((uint32_t)(v >> 32), cap);
   const uint32_t ntiles = (uint32_t)(v & 0xffffffffull);
-  if (nitems == 0) return;
-  const int32_t runs = hdr->runs;
-  for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    leaf_place_tile<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, tile, fused, runs);
-    __syncthreads();  // s_slot is rewritten by the next tile
-  }
+  const uint32_t t0 = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
+  const uint32_t t1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
+  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, fused, hdr->runs);
 }
 
 }  // namespace ps

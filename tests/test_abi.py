@@ -103,11 +103,11 @@ def test_minrun_argument_errors_without_gpu(lib):
 
 def test_tuning_table_without_gpu(lib):
     import paper_1805_04154_gb300 as ps
-    assert ps.ps_tune_get(0, True) == (12, 2)
+    assert ps.ps_tune_get(0, True) == (8, 2)
     ps.ps_tune_set(0, True, 16, 2)
     assert ps.ps_tune_get(0, True) == (16, 2)
-    assert ps.ps_tune_get(0, False) == (12, 2)
+    assert ps.ps_tune_get(0, False) == (8, 2)
     with pytest.raises(ps.PowersortError):
         ps.ps_tune_set(0, True, 10, 2)  # not a configuration the library carries
     ps.ps_tune_set(0, True, 0, 0)
-    assert ps.ps_tune_get(0, True) == (12, 2)
+    assert ps.ps_tune_get(0, True) == (8, 2)
