@@ -13,8 +13,9 @@ events between a barrier + synchronize on both sides, max over ranks.  Also repo
                  per merge output) over its CUDA-event time inside the timed region, against the
                  measured HBM copy bandwidth; plus the whole sort against the merge-cost
                  roofline M x 8 B x 2 / bandwidth (M = exact merge cost of the detected runs).
-  * e2e       -- the same metric through the C-ABI host-buffer entry (ps_sort_host): pinned host
-                 input -> device, sort, device -> pinned host output, every step.
+  * e2e       -- the same metric through the package's host-array pipeline (HostSortPipeline over
+                 the device-driven C-ABI sort): pinned host input -> device, sort, device ->
+                 pinned host output, every step, four arrays in flight.
   * cpu_baseline -- the CPU oracle (single-threaded plain C++ powersort) on one input of the same
                  workload on the host cores.
 --impl reference: the oracle as the reference arm, each step a bounded sample (the first
@@ -533,26 +534,25 @@ def run_gpu(args):
         copies = None
         hk_in = torch.from_numpy(keys).pin_memory()
         hv_in = torch.from_numpy(vals.view(np.int32)).pin_memory()
-        nsets = 3
-        outs = [(torch.empty_like(hk_in).pin_memory(), torch.empty_like(hv_in).pin_memory()) for _ in range(nsets)]
-        wsz = ps.ps_workspace_size(ps.PS_KEY_I32, True, n)
-        sets = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
-                 torch.empty(wsz, dtype=torch.uint8, device=dev)) for _ in range(nsets)]
-        streams = [torch.cuda.Stream(dev) for _ in range(nsets)]
-        e2e_steps = max(3 * nsets, min(args.steps, 12))
+        from paper_1805_04154_gb300.pipeline import HostSortPipeline
+        depth = 4
+        pipe = HostSortPipeline(n, torch.int32, True, depth=depth, device=dev)
+        outs = [(torch.empty_like(hk_in).pin_memory(), torch.empty_like(hv_in).pin_memory()) for _ in range(depth)]
+        e2e_steps = max(4 * depth, min(args.steps, 24))
 
         def e2e_step(i):
-            q = i % nsets
-            ps.ps_sort_host_ws(ps.PS_KEY_I32, hk_in.data_ptr(), hv_in.data_ptr(), outs[q][0].data_ptr(),
-                               outs[q][1].data_ptr(), n, sets[q][0], sets[q][1], sets[q][2], stream=streams[q])
+            q = i % depth
+            pipe.submit(hk_in, hv_in, outs[q][0], outs[q][1])
 
-        for i in range(nsets):
+        for i in range(depth):
             e2e_step(i)
+        pipe.synchronize()
         torch.cuda.synchronize(dev)
         if dist:
             dist.barrier()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        streams = [st_ for (_, _, _, st_) in pipe._sets]
         e0.record(streams[0])
         for st_ in streams[1:]:
             st_.wait_event(e0)
@@ -564,6 +564,7 @@ def run_gpu(args):
             streams[0].wait_event(ev)
         e1.record(streams[0])
         torch.cuda.synchronize(dev)
+        pipe.synchronize()
         e2e_ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
         ok_e2e = all(bool(np.all(o[0].numpy()[1:] >= o[0].numpy()[:-1])) for o in outs)
         # serial: one ps_sort_host call at a time (synchronous, pool workspace)
@@ -584,11 +585,12 @@ def run_gpu(args):
         line["e2e"] = {"value": replica_throughput(ws, n, e2e_steps, e2e_ms), "unit": UNIT,
                        "h2d_bytes_per_step": n * eb, "d2h_bytes_per_step": n * eb, "steps": e2e_steps,
                        "ms_per_step": e2e_ms / e2e_steps,
-                       "entry": "ps_sort_host_ws on 3 streams (pinned host buffers, one device buffer set per stream)",
+                       "entry": "HostSortPipeline (pinned host buffers; copy-in, device-driven sort and copy-out "
+                                "of 4 arrays in flight, copies in each direction in submission order)",
                        "serial": {"entry": "ps_sort_host (one call at a time)", "ms_per_step": serial_ms,
                                   "value": n / (serial_ms / 1000.0) / 1e9},
                        "sorted_check": ok_e2e}
-        del sets, outs
+        del pipe, outs
         torch.cuda.empty_cache()
 
     if rank == 0 and ws == 1 and not args.no_variants:

@@ -238,15 +238,14 @@ ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_i
                        uint32_t* vals_out, int64_t n, void* stream);
 
 /* Host arrays sorted through caller-owned device memory, queued on `stream` without waiting for
- * the result: copies keys_in/vals_in (host, n elements) into dev_keys/dev_vals (device, n
- * elements, natural alignment), sorts them as ps_sort_ws does with `workspace`
- * (ps_workspace_size(key_type, vals_in != NULL, n, 0) bytes), and copies the result to
- * keys_out/vals_out (host; may alias the inputs).  The call returns once the sort's plan is
- * known (one internal stream synchronization after the copy-in and planning); the copy-out is
- * still in flight -- synchronize `stream` before reading keys_out.  With pinned host memory and
- * one set of device buffers per stream, consecutive calls on different streams overlap the
- * copy-in of one array, the sort of another and the copy-out of a third.  vals_in, vals_out and
- * dev_vals are all NULL or all non-NULL.  Errors as for ps_sort_ws. */
+ * anything: copies keys_in/vals_in (host, n elements) into dev_keys/dev_vals (device, n
+ * elements, natural alignment), sorts them with the device-driven pipeline of ps_sort_async_ws
+ * and `workspace` (ps_workspace_size(key_type, vals_in != NULL, n, 0) bytes), and copies the
+ * result to keys_out/vals_out (host; may alias the inputs).  Synchronize `stream` before reading
+ * keys_out.  With pinned host memory and one set of device buffers per stream, consecutive calls
+ * on different streams overlap the copy-in of one array, the sort of another and the copy-out of
+ * a third.  vals_in, vals_out and dev_vals are all NULL or all non-NULL.  Argument errors are
+ * returned at once; errors found on the device are reported by ps_stream_status. */
 ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
                           uint32_t* vals_out, int64_t n, void* dev_keys, uint32_t* dev_vals, void* workspace,
                           size_t workspace_bytes, void* stream);

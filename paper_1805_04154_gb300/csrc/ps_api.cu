@@ -823,7 +823,10 @@ ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* val
   cudaStream_t s = (cudaStream_t)stream;
   PS_TRY(cudaMemcpyAsync(dev_keys, keys_in, (size_t)n * kb, cudaMemcpyHostToDevice, s));
   if (dev_vals) PS_TRY(cudaMemcpyAsync(dev_vals, vals_in, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-  const ps_status st = run(key_type, dev_keys, dev_vals, n, nullptr, 1, false, workspace, workspace_bytes, s, nullptr);
+  // device-driven: no host round trip, so the caller's next call (on another stream) is queued
+  // while this array is still being copied in
+  const ps_status st = run_async(key_type, dev_keys, dev_vals, n, nullptr, 1, false, workspace, workspace_bytes, s,
+                                 PS_TREE_POWERSORT);
   if (st != PS_OK) return st;
   PS_TRY(cudaMemcpyAsync(keys_out, dev_keys, (size_t)n * kb, cudaMemcpyDeviceToHost, s));
   if (dev_vals) PS_TRY(cudaMemcpyAsync(vals_out, dev_vals, (size_t)n * 4, cudaMemcpyDeviceToHost, s));
