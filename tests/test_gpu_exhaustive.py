@@ -4,7 +4,9 @@ composition of 12 into run lengths (2^11 arrays, ascending runs separated by dro
 with descending runs) -- output and payload bit-exact, run starts, directions, node powers, leaf
 depths and merge cost equal.  Plus structural properties of the device tree: powers in
 [1, floor(lg n_seg) + 1], adjacent powers differ, a node's parent has the smaller power, and on
-random permutations powersort's and peeksort's merge costs are within 1.5% of each other."""
+random permutations powersort's and peeksort's merge costs are within 1.5% of each other.  The
+same relation patterns and compositions with runs extended to a minimal length w (Sec. 5.1)
+match the oracle's minimal-run-length powersort array by array."""
 import itertools
 
 import numpy as np
@@ -123,3 +125,44 @@ def test_bounded_wait_timeout_reported_and_device_usable(ps):
     ps.ps_sort(dk, dv, key_type=0)
     assert ps.ps_stream_status() == 0
     np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
+
+
+def _check_batch_minrun(ps, arrays, w):
+    """All arrays as segments of one minimal-run-length call, against the oracle per array."""
+    off = np.zeros(len(arrays) + 1, np.int64)
+    off[1:] = np.cumsum([a.size for a in arrays])
+    keys = np.concatenate(arrays).astype(np.int32)
+    vals = np.arange(keys.size, dtype=np.uint32)
+    exp_s, exp_d, exp_ld, exp_k, exp_v, cost = [], [], [], [], [], 0
+    for i, a in enumerate(arrays):
+        ref = oracle.powersort(a, vals[off[i]:off[i + 1]], min_run=w)
+        exp_s.append(ref.starts[:-1] + off[i])
+        exp_d.append(ref.desc)
+        exp_ld.append(ref.leaf_depth)
+        exp_k.append(ref.keys)
+        exp_v.append(ref.vals)
+        cost += ref.cost
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    doff = torch.from_numpy(off).cuda()
+    an = ps.ps_analyze(dk, offsets=doff, key_type=0, min_run=w)
+    np.testing.assert_array_equal(an["starts"], np.concatenate(exp_s + [np.array([keys.size])]))
+    np.testing.assert_array_equal(an["desc"] & 1, np.concatenate(exp_d))
+    np.testing.assert_array_equal(an["leaf_depth"].astype(np.int32), np.concatenate(exp_ld))
+    assert an["cost"] == cost
+    ws = torch.empty(ps.ps_workspace_size(0, True, keys.size, True), dtype=torch.uint8, device="cuda")
+    ps.ps_sort_minrun_ws(dk, dv, ws, w, offsets=doff, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), np.concatenate(exp_k))
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), np.concatenate(exp_v))
+
+
+@pytest.mark.parametrize("w", [2, 3, 4, 5, 8])
+def test_all_relation_patterns_minrun(ps, w):
+    """Every relation pattern of 2 <= n <= 8 with runs extended to w (Sec. 5.1): partition,
+    directions, tree, cost and output equal to the oracle's for each array."""
+    _check_batch_minrun(ps, _relation_arrays(), w)
+
+
+@pytest.mark.parametrize("w", [3, 5, 12])
+def test_all_compositions_of_12_minrun(ps, w):
+    _check_batch_minrun(ps, _composition_arrays(), w)
