@@ -226,6 +226,14 @@ ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int
                             uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
                             int32_t* node_left, int32_t* node_right, uint8_t* node_depth, void* stream);
 
+/* Bounds-checked builds.  A library compiled with -DPS_DEBUG (libpowersort_debug.so) compares
+ * the data-derived indices of its kernels (shared-memory slots of the subtree merges, stage
+ * offsets of the level passes, words of the node-power array, tree outputs, transfer-table
+ * states) with their extents, skips any access out of range and counts it.  *hits receives the
+ * count since the library was loaded (synchronize the sorting streams first).  PS_ERR_UNSUPPORTED
+ * from a library built without the checks. */
+ps_status ps_debug_bounds(unsigned long long* hits);
+
 /* Plan statistics of one array (keys on the device, not modified; workspace from the pool).
  * Synchronizes the stream. */
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream);

@@ -34,7 +34,8 @@ _STATUS = {0: "PS_OK", 1: "PS_ERR_INVALID_ARG", 2: "PS_ERR_UNSUPPORTED", 3: "PS_
            4: "PS_ERR_CUDA", 5: "PS_ERR_TIMEOUT", 6: "PS_ERR_INTERNAL"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-lib_path = os.path.join(_HERE, "libpowersort.so")
+# PS_DEBUG=1 selects the bounds-checked build (libpowersort_debug.so, see _build.build(debug=True))
+lib_path = os.path.join(_HERE, "libpowersort_debug.so" if os.environ.get("PS_DEBUG") == "1" else "libpowersort.so")
 _lib = None
 _lock = threading.Lock()
 
@@ -97,6 +98,7 @@ def load():
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
                 "ps_sort_minrun_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+                "ps_debug_bounds": ([vp], i32),
                 "ps_analyze_minrun": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                        vp], i32),
             }
@@ -313,6 +315,17 @@ def ps_sort_stats(keys: torch.Tensor, key_type: int | None = None, stream=None) 
     _check(load().ps_sort_stats(kt, _dev_ptr(keys, "keys"), keys.numel(), ctypes.byref(st),
                                 _stream_ptr(stream, keys.device)), "ps_sort_stats")
     return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+
+def ps_debug_bounds() -> int | None:
+    """Out-of-range accesses counted by a bounds-checked library (None for a library built
+    without the checks)."""
+    v = ctypes.c_ulonglong(0)
+    st = load().ps_debug_bounds(ctypes.byref(v))
+    if st == 2:
+        return None
+    _check(st, "ps_debug_bounds")
+    return int(v.value)
 
 
 def ps_stream_status(stream=None, device=None) -> int:

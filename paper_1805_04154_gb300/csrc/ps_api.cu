@@ -13,6 +13,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "powersort.h"
+#include "ps_debug.cuh"
 #include "ps_internal.h"
 
 namespace {
@@ -783,6 +784,19 @@ ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int
   const bool seg = d_offsets != nullptr;
   return run(key_type, const_cast<void*>(keys), nullptr, n, d_offsets, seg ? count : 1, seg, workspace,
              workspace_bytes, (cudaStream_t)stream, &an, PS_TREE_POWERSORT, min_run);
+}
+
+ps_status ps_debug_bounds(unsigned long long* hits) {
+  if (!hits) return PS_ERR_INVALID_ARG;
+  if (!kBoundsChecked) return PS_ERR_UNSUPPORTED;
+  const unsigned long long parts[3] = {bounds_hits_meta(), bounds_hits_keys32(), bounds_hits_keys64()};
+  unsigned long long sum = 0;
+  for (unsigned long long x : parts) {
+    if (x == ~0ull) return PS_ERR_CUDA;
+    sum += x;
+  }
+  *hits = sum;
+  return PS_OK;
 }
 
 ps_status ps_sort_stats(int key_type, const void* keys, int64_t n, ps_stats* out, void* stream) {

@@ -25,6 +25,7 @@
 #pragma once
 
 #include "ps_common.cuh"
+#include "ps_debug.cuh"
 #include "ps_detect.cuh"
 #include "ps_internal.h"
 
@@ -187,7 +188,7 @@ __device__ __forceinline__ void mr_warp_compose(const uint16_t (*tab)[kMrStates]
     uint32_t st = (uint32_t)x, cnt = 0;
 #pragma unroll 4
     for (int i = 0; i < 32; ++i) {
-      const uint32_t e = tab[i][st];
+      const uint32_t e = PS_IN_RANGE(st, kMrStates) ? tab[i][st] : 0u;
       cnt += e >> 6;
       st = e & 63u;
     }

@@ -95,4 +95,10 @@ cudaError_t launch_header_out(const Ctx& c, PlanHeader* mapped);
 cudaError_t launch_status_out(const Ctx& c);
 cudaError_t launch_wait_timeout_probe(uint32_t polls, uint32_t* lib_status, cudaStream_t s);
 
+// Bounds-checked builds (-DPS_DEBUG): out-of-range accesses counted by each translation unit's
+// kernels (0 in other builds).
+unsigned long long bounds_hits_meta();
+unsigned long long bounds_hits_keys32();
+unsigned long long bounds_hits_keys64();
+
 }  // namespace ps

@@ -5,4 +5,5 @@ namespace ps {
 const KeyLaunch kLaunchI32 = Launch<KeyI32>::table();
 const KeyLaunch kLaunchU32 = Launch<KeyU32>::table();
 const KeyLaunch kLaunchF32 = Launch<KeyF32>::table();
+unsigned long long bounds_hits_keys32() { return bounds_hits_here(); }
 }  // namespace ps

@@ -3,4 +3,5 @@
 
 namespace ps {
 const KeyLaunch kLaunchU64 = Launch<KeyU64>::table();
+unsigned long long bounds_hits_keys64() { return bounds_hits_here(); }
 }  // namespace ps

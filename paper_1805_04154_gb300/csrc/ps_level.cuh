@@ -4,6 +4,7 @@
 #pragma once
 
 #include "ps_common.cuh"
+#include "ps_debug.cuh"
 #include "ps_mergeutil.cuh"
 
 namespace ps {
@@ -423,13 +424,16 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           for (int q = 0; q < IPT; ++q) {
             const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
             key[q] = takeA ? a : b;
-            if (V) val[q] = sv[takeA ? d.vaoff + i : d.vboff + j];
+            if (V) {
+              const int32_t vi = takeA ? d.vaoff + i : d.vboff + j;
+              val[q] = PS_IN_RANGE(vi, Lay::VCAP) ? sv[vi] : 0u;
+            }
             i += takeA ? 1 : 0;
             j += takeA ? 0 : 1;
             if (takeA) {
-              if (i < la) a = A[i];
+              if (i < la && PS_IN_RANGE(d.aoff + i, Lay::KCAP)) a = A[i];
             } else {
-              if (j < lb) b = B[j];
+              if (j < lb && PS_IN_RANGE(d.boff + j, Lay::KCAP)) b = B[j];
             }
           }
         } else {
@@ -438,13 +442,16 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             if (q < cnt) {
               const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
               key[q] = takeA ? a : b;
-              if (V) val[q] = sv[takeA ? d.vaoff + i : d.vboff + j];
+              if (V) {
+              const int32_t vi = takeA ? d.vaoff + i : d.vboff + j;
+              val[q] = PS_IN_RANGE(vi, Lay::VCAP) ? sv[vi] : 0u;
+            }
               i += takeA ? 1 : 0;
               j += takeA ? 0 : 1;
               if (takeA) {
-                if (i < la) a = A[i];
+                if (i < la && PS_IN_RANGE(d.aoff + i, Lay::KCAP)) a = A[i];
               } else {
-                if (j < lb) b = B[j];
+                if (j < lb && PS_IN_RANGE(d.boff + j, Lay::KCAP)) b = B[j];
               }
             }
           }

@@ -16,6 +16,7 @@
 #pragma once
 
 #include "ps_common.cuh"
+#include "ps_debug.cuh"
 #include "ps_mergeutil.cuh"
 
 namespace ps {
@@ -49,8 +50,10 @@ struct SubElem<K, 4> {
     uint64_t* w;
   };
   __device__ __forceinline__ static Arr arr(uint8_t* base) { return Arr{(uint64_t*)base}; }
-  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) { return a.w[i]; }
-  __device__ __forceinline__ static void st(const Arr& a, int32_t i, R x) { a.w[i] = x; }
+  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) { return PS_IN_RANGE(i, kPadded) ? a.w[i] : R(0); }
+  __device__ __forceinline__ static void st(const Arr& a, int32_t i, R x) {
+    if (PS_IN_RANGE(i, kPadded)) a.w[i] = x;
+  }
   __device__ __forceinline__ static R make(uint32_t key, int32_t pos) {
     return ((uint64_t)K::ord(key) << 32) | (uint32_t)pos;
   }
@@ -78,8 +81,11 @@ struct SubElem<K, 8> {
   __device__ __forceinline__ static Arr arr(uint8_t* base) {
     return Arr{(uint64_t*)base, (uint32_t*)(base + (size_t)kPadded * 8)};
   }
-  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) { return R{a.k[i], a.p[i]}; }
+  __device__ __forceinline__ static R ld(const Arr& a, int32_t i) {
+    return PS_IN_RANGE(i, kPadded) ? R{a.k[i], a.p[i]} : R{0, 0};
+  }
   __device__ __forceinline__ static void st(const Arr& a, int32_t i, R x) {
+    if (!PS_IN_RANGE(i, kPadded)) return;
     a.k[i] = x.k;
     a.p[i] = x.p;
   }
@@ -221,7 +227,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
           const R x = E::ld(X, sub_slot<E>(p));
           int32_t rank = rs[k];
           for (int32_t j = rs[k]; j < rs[k + 1]; ++j) rank += E::less(E::ld(X, sub_slot<E>(j)), x) ? 1 : 0;
-          src[rank] = (int16_t)p;
+          if (PS_IN_RANGE(rank, TS)) src[rank] = (int16_t)p;
         }
       }
     }
@@ -246,7 +252,8 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
         if (p < m) {
           while (p >= rs[k + 1]) ++k;
           if (rdsc[k] != 0) {
-            const int32_t from = (rdsc[k] & 2) ? (int32_t)src[p] : (int32_t)rs[k] + rs[k + 1] - 1 - p;
+            const int32_t from = (rdsc[k] & 2) ? (PS_IN_RANGE(p, TS) ? (int32_t)src[p] : p)
+                                               : (int32_t)rs[k] + rs[k + 1] - 1 - p;
             if (from != p) {
               v[q] = E::ld(X, sub_slot<E>(from));
               mv |= 1u << q;
@@ -318,7 +325,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
       const int32_t at = s_cnt[warp][rd] + __popc(peers & lt_mask);
       const uint32_t nlo = (uint32_t)(S[nodeL[j]] - lo), nmid = (uint32_t)(S[j] - lo);
       const uint32_t nhi = (uint32_t)(S[nodeR[j]] - lo);
-      ent[at] = (uint64_t)(nlo | (nmid << 16)) | ((uint64_t)nhi << 32);
+      if (PS_IN_RANGE(at, RC)) ent[at] = (uint64_t)(nlo | (nmid << 16)) | ((uint64_t)nhi << 32);
     }
     __syncwarp();
     if (k < w1 && lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
@@ -414,7 +421,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
       if (p < m) {
         const R x = E::ld(X, sub_slot<E>(p));
         ok[lo + p] = E::key(x);
-        ov[lo + p] = pay[E::pos(x)];
+        ov[lo + p] = PS_IN_RANGE(E::pos(x), m) ? pay[E::pos(x)] : 0u;
       }
     }
   } else {

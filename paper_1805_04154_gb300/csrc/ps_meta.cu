@@ -1,5 +1,6 @@
 // Stages 2-3 and planning: node powers, the merge tree as nearest smaller values of the powers,
 // node/leaf depths, merge cost, and the work lists of stage 4.  Key-independent; O(r) work.
+#include "ps_debug.cuh"
 #include "ps_internal.h"
 #include "ps_level.cuh"
 
@@ -90,8 +91,10 @@ constexpr uint32_t kNoPower = 0xFFu;  // staged power of a virtual index past r
 __device__ __forceinline__ uint32_t load_power_window(const uint8_t* __restrict__ P, int32_t r, int32_t b) {
   const uint32_t* __restrict__ Pw = (const uint32_t*)P;
   const int32_t wa = b >> 2;  // floor(b / 4), also for negative b
-  const uint32_t lo = (wa >= 0 && 4 * wa <= r) ? Pw[wa] : 0u;
-  const uint32_t hi = ((b & 3) != 0 && wa + 1 >= 0 && 4 * (wa + 1) <= r) ? Pw[wa + 1] : 0u;
+  const int32_t words = r / 4 + 1;  // words holding bytes 0..r
+  const uint32_t lo = (wa >= 0 && 4 * wa <= r && PS_IN_RANGE(wa, words)) ? Pw[wa] : 0u;
+  const uint32_t hi =
+      ((b & 3) != 0 && wa + 1 >= 0 && 4 * (wa + 1) <= r && PS_IN_RANGE(wa + 1, words)) ? Pw[wa + 1] : 0u;
   uint32_t w = __funnelshift_r(lo, hi, (uint32_t)(b & 3) * 8u);
   if (b < 0 || b + 3 > r) {
 #pragma unroll
@@ -295,6 +298,7 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
       const uint32_t cnt = (sp[(i >> 2) + (i >> 5)] >> (8 * (i & 3))) & 0xFFu;
       if (cnt != 0xFFu) {
         const int32_t j = virt_to_j<kBackward>(u, r);
+        if (!PS_IN_RANGE(j, r + 1)) continue;
         near_out[j] = virt_to_j<kBackward>(s_near[i + (i >> 5)], r);
         if (kBackward) depth_acc[j] = (uint8_t)(depth_acc[j] + cnt);
         else depth_acc[j] = (uint8_t)cnt;
@@ -677,4 +681,8 @@ cudaError_t launch_check_offsets(const Ctx& c) {
   return cudaGetLastError();
 }
 
+}  // namespace ps
+
+namespace ps {
+unsigned long long bounds_hits_meta() { return bounds_hits_here(); }
 }  // namespace ps

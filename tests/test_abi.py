@@ -101,6 +101,12 @@ def test_minrun_argument_errors_without_gpu(lib):
                                      None, None, None, None, None) == 1
 
 
+def test_release_build_has_no_bounds_checks(lib):
+    import paper_1805_04154_gb300 as ps
+    if ps.lib_path.endswith("libpowersort.so"):
+        assert ps.ps_debug_bounds() is None  # PS_ERR_UNSUPPORTED without -DPS_DEBUG
+
+
 def test_tuning_table_without_gpu(lib):
     import paper_1805_04154_gb300 as ps
     assert ps.ps_tune_get(0, True) == (8, 2)
