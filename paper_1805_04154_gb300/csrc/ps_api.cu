@@ -148,12 +148,36 @@ constexpr int kStages = 8;  // 0 detect, 1 powers+tree+plan, 2 SMEM subtrees, 3 
 std::atomic<int> g_prof_on{0};
 std::atomic<unsigned long long> g_launches{0};
 struct ProfRec {
-  int stage;
+  int stage, dev;
   cudaEvent_t a, b;
   uint64_t bytes, launches;
 };
 std::mutex g_prof_mu;
 std::vector<ProfRec> g_prof_pending;
+// Events are reused across sorts (creating one per stage would put host time between the
+// plan read-back and the merge launches of every profiled sort).
+std::vector<cudaEvent_t> g_ev_free[kMaxDevices];
+
+cudaEvent_t prof_event(int dev) {
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (dev >= 0 && dev < kMaxDevices && !g_ev_free[dev].empty()) {
+      cudaEvent_t e = g_ev_free[dev].back();
+      g_ev_free[dev].pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// with g_prof_mu held
+void prof_release(int dev, cudaEvent_t e) {
+  if (!e) return;
+  if (dev >= 0 && dev < kMaxDevices) g_ev_free[dev].push_back(e);
+  else cudaEventDestroy(e);
+}
 double g_prof_ms[kStages] = {};
 uint64_t g_prof_launch[kStages] = {}, g_prof_bytes[kStages] = {};
 
@@ -164,12 +188,13 @@ const char* const kStageNames[kStages] = {"ps:detect", "ps:meta", "ps:subtree_sm
 
 struct StageTimer {
   int stage;
+  int dev = 0;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
   bool on;
   StageTimer(int st, cudaStream_t strm) : stage(st), s(strm), on(g_prof_on.load() != 0) {
     nvtxRangePushA(kStageNames[st]);
-    if (on && cudaEventCreate(&a) == cudaSuccess) cudaEventRecord(a, s);
+    if (on && cudaGetDevice(&dev) == cudaSuccess && (a = prof_event(dev)) != nullptr) cudaEventRecord(a, s);
     else on = false;
   }
   ~StageTimer() { nvtxRangePop(); }
@@ -178,14 +203,14 @@ struct StageTimer {
   void done(uint64_t bytes, uint64_t launches) {
     g_launches += launches;
     if (!on) return;
-    cudaEvent_t b = nullptr;
-    if (cudaEventCreate(&b) != cudaSuccess) {
-      cudaEventDestroy(a);
+    cudaEvent_t b = prof_event(dev);
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!b) {
+      prof_release(dev, a);
       return;
     }
     cudaEventRecord(b, s);
-    std::lock_guard<std::mutex> lk(g_prof_mu);
-    g_prof_pending.push_back(ProfRec{stage, a, b, bytes, launches});
+    g_prof_pending.push_back(ProfRec{stage, dev, a, b, bytes, launches});
   }
 };
 
@@ -895,8 +920,9 @@ ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_i
 ps_status ps_profile_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto& p : g_prof_pending) {
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    cudaEventSynchronize(p.b);  // the events are reused
+    prof_release(p.dev, p.a);
+    prof_release(p.dev, p.b);
   }
   g_prof_pending.clear();
   for (int i = 0; i < kStages; ++i) {
@@ -919,8 +945,8 @@ ps_status ps_profile_read(ps_profile* out) {
     g_prof_ms[p.stage] += ms;
     g_prof_launch[p.stage] += p.launches;
     g_prof_bytes[p.stage] += p.bytes;
-    cudaEventDestroy(p.a);
-    cudaEventDestroy(p.b);
+    prof_release(p.dev, p.a);
+    prof_release(p.dev, p.b);
   }
   g_prof_pending.clear();
   for (int i = 0; i < kStages; ++i) {
