@@ -263,22 +263,35 @@ minrun_group_kernel(const uint32_t* __restrict__ tile_tab, int32_t ntiles, int w
   }
 }
 
-// Pass 3 (one thread): the groups walked from F(0) at position 0.  grp_pre[g] = entry state of
-// group g | runs before it << 8; hdr->runs = r and S[r] = n.
-static __global__ void minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int32_t n,
-                                         uint64_t* __restrict__ grp_pre, int32_t* __restrict__ S,
-                                         PlanHeader* __restrict__ hdr) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  uint32_t st = 0, cnt = 0;
-  for (int32_t g = 0; g < ngroups; ++g) {
-    grp_pre[g] = (uint64_t)st | ((uint64_t)cnt << 8);
-    const uint32_t e = grp_tab[(size_t)g * kMrStates + st];
-    cnt += e >> 6;
-    st = e & 63u;
+// Pass 3 (one CTA): the groups walked from F(0) at position 0, their tables staged in shared
+// memory kMrTopChunk groups at a time (one coalesced load per chunk instead of a dependent global
+// load per group).  grp_pre[g] = entry state of group g | runs before it << 8; hdr->runs = r and
+// S[r] = n.
+constexpr int kMrTopChunk = 64;
+static __global__ void __launch_bounds__(256)
+minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int32_t n, uint64_t* __restrict__ grp_pre,
+                  int32_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
+  __shared__ uint32_t s_t[kMrTopChunk * kMrStates];
+  uint32_t st = 0, cnt = 0;  // meaningful in thread 0
+  for (int32_t g0 = 0; g0 < ngroups; g0 += kMrTopChunk) {
+    const int32_t ng = min(kMrTopChunk, ngroups - g0);
+    for (int i = threadIdx.x; i < ng * kMrStates; i += blockDim.x) s_t[i] = grp_tab[(size_t)g0 * kMrStates + i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int32_t g = 0; g < ng; ++g) {
+        grp_pre[g0 + g] = (uint64_t)st | ((uint64_t)cnt << 8);
+        const uint32_t e = PS_IN_RANGE(st, kMrStates) ? s_t[g * kMrStates + st] : 0u;
+        cnt += e >> 6;
+        st = e & 63u;
+      }
+    }
+    __syncthreads();
   }
-  hdr->runs = (int32_t)cnt;
-  if (cnt <= (uint32_t)n) S[cnt] = n;
-  else post_status(&hdr->status, nullptr, kDevInternal);  // a run has at least one element
+  if (threadIdx.x == 0) {
+    hdr->runs = (int32_t)cnt;
+    if (cnt <= (uint32_t)n) S[cnt] = n;
+    else post_status(&hdr->status, nullptr, kDevInternal);  // a run has at least one element
+  }
 }
 
 // Pass 4: the entry state and run count of every tile of a group.

@@ -37,7 +37,7 @@ struct Launch {
     minrun_reduce_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>((const T*)c.k[0], c.n, c.offsets, c.count,
                                                                     c.min_run, c.mr_tile_tab, c.thr_L, c.thr_F);
     minrun_group_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.min_run, c.mr_grp_tab);
-    minrun_top_kernel<<<1, 32, 0, c.stream>>>(c.mr_grp_tab, groups, c.n, c.mr_grp_pre, c.S, c.hdr);
+    minrun_top_kernel<<<1, 256, 0, c.stream>>>(c.mr_grp_tab, groups, c.n, c.mr_grp_pre, c.S, c.hdr);
     minrun_tile_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.mr_grp_pre, tile_pre);
     minrun_emit_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>(c.n, c.offsets, c.count, c.min_run, tile_pre,
                                                                   c.thr_L, c.thr_F, nthreads, c.S, c.run_desc,
