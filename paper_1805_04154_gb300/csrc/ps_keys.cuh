@@ -72,7 +72,7 @@ struct Launch {
     }
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     if (ntasks == kCountOnDevice)
-      subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 3, kSubThreads, bytes, c.stream>>>(
+      subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 4, kSubThreads, bytes, c.stream>>>(
           b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)(c.n + 2),
           c.fused ? 1 : 0, c.hdr, c.lib_status);
     else

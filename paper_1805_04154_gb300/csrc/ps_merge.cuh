@@ -446,7 +446,7 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
 // A persistent grid over the task count the plan left on the device (no host round trip); the
 // loop state costs registers, so it is sized for 3 CTAs per SM.
 template <class K, bool V>
-__global__ void __launch_bounds__(kSubThreads, 3)
+__global__ void __launch_bounds__(kSubThreads, 4)
 subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                           const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                           const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
