@@ -105,7 +105,7 @@ struct ThreadRuns {
     F = 0;
     if (nvalid == 0) return;
     T prev = (p0 > 0) ? keys[p0 - 1] : (T)0;
-    if (p0 + kDetectItems < n && ((uintptr_t)(keys + p0) & 15u) == 0) {
+    if (kDetectItems < n - p0 && ((uintptr_t)(keys + p0) & 15u) == 0) {
       constexpr int kPer = 16 / (int)sizeof(T);
       const uint4* src = reinterpret_cast<const uint4*>(keys + p0);
 #pragma unroll
@@ -126,7 +126,7 @@ struct ThreadRuns {
         L |= (uint64_t)(K::ord(prev) <= K::ord(cur)) << q;
         prev = cur;
       }
-      if (p0 + kDetectItems < n) L |= (uint64_t)(K::ord(prev) <= K::ord(keys[p0 + kDetectItems])) << kDetectItems;
+      if (kDetectItems < n - p0) L |= (uint64_t)(K::ord(prev) <= K::ord(keys[p0 + kDetectItems])) << kDetectItems;
     }
     if (p0 == 0) F |= 1ull;
     if (offsets != nullptr) {

@@ -109,7 +109,8 @@ __device__ __forceinline__ void chunk16(const E* base, int32_t e0, int32_t e1, i
   constexpr int kPer = 16 / (int)sizeof(E);
   const int32_t phase = (int32_t)(((uintptr_t)base & 15u) / sizeof(E));  // elements before base in its block
   c0 = ((e0 + phase) & ~(kPer - 1)) - phase;
-  c1 = (e1 > e0) ? (((e1 + phase + kPer - 1) & ~(kPer - 1)) - phase) : c0;
+  // in 64 bits: e1 may lie within a few elements of 2^31
+  c1 = (e1 > e0) ? (int32_t)((((int64_t)e1 + phase + kPer - 1) & ~(int64_t)(kPer - 1)) - phase) : c0;
 }
 
 __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
@@ -214,7 +215,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
               ai = 0;
               m_new[m] = true;
             }
-            const int32_t g1 = min(cnd.z, (cg0 / kTile + 1) * kTile);
+            const int32_t g1 = (int32_t)min((int64_t)cnd.z, ((int64_t)(cg0 / kTile) + 1) * kTile);
             const int32_t cla = cnd.y - cnd.x, clb = cnd.z - cnd.y, diag = g1 - cnd.x;
             m_nd[m] = cnd;
             m_slot[m] = cs;

@@ -481,7 +481,8 @@ __device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restri
   if (out_buffer(ldepth[i], fused != 0) == 1) {
     T* __restrict__ k1 = (T*)buf.k[1];
     uint32_t* __restrict__ v1 = buf.v[1];
-    const int32_t q0 = s + (int32_t)k * kMergeTile + threadIdx.x, q1 = min(e, s + ((int32_t)k + 1) * kMergeTile);
+    const int32_t q0 = s + (int32_t)k * kMergeTile + threadIdx.x;
+    const int32_t q1 = (int32_t)min((int64_t)e, (int64_t)s + ((int64_t)k + 1) * kMergeTile);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int32_t q = q0 + u * 256;
@@ -503,7 +504,8 @@ __device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restri
     T* kk = (T*)buf.k[0];
     uint32_t* vv = buf.v[0];
     const int32_t half = (e - s) / 2;
-    const int32_t p0 = s + (int32_t)k * kMergeTile + threadIdx.x, p1 = min(s + half, s + ((int32_t)k + 1) * kMergeTile);
+    const int32_t p0 = s + (int32_t)k * kMergeTile + threadIdx.x;
+    const int32_t p1 = (int32_t)min((int64_t)s + half, (int64_t)s + ((int64_t)k + 1) * kMergeTile);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
       const int32_t p = p0 + u * 256;

@@ -452,8 +452,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         if (run_desc[x] & 2) post_status(&hdr->status, nullptr, kDevInternal);  // extended runs are short
         uint32_t tiles = 0;
         const bool odd_buf = out_buffer(d, fused != 0) == 1;
-        if (odd_buf) tiles = (uint32_t)((len + kMergeTile - 1) / kMergeTile);
-        else if (desc) tiles = (uint32_t)((len / 2 + kMergeTile - 1) / kMergeTile);
+        if (odd_buf) tiles = (uint32_t)(((int64_t)len + kMergeTile - 1) / kMergeTile);
+        else if (desc) tiles = (uint32_t)(((int64_t)len / 2 + kMergeTile - 1) / kMergeTile);
         if (tiles) {
           const unsigned long long old = atomicAdd(&hdr->leaf_ctr, (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
