@@ -150,6 +150,46 @@ def _dev_ptr(t: torch.Tensor | None, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
+_KEY_BYTES = {PS_KEY_I32: 4, PS_KEY_U32: 4, PS_KEY_U64: 8, PS_KEY_F32: 4}
+
+
+def _key_type(keys: torch.Tensor, key_type: int | None) -> int:
+    """The key type passed to the library: the dtype's, or the caller's choice when its key width
+    matches the tensor's elements (the library reads n keys of that width from the pointer)."""
+    kt = key_type_of(keys) if key_type is None else int(key_type)
+    if kt not in _KEY_BYTES:
+        raise ValueError(f"unknown key type {kt}")
+    if keys.element_size() != _KEY_BYTES[kt]:
+        raise ValueError(f"key type {kt} reads {_KEY_BYTES[kt]}-byte keys but keys are {keys.dtype}")
+    return kt
+
+
+def _check_vals(vals: torch.Tensor | None, keys: torch.Tensor) -> None:
+    if vals is None:
+        return
+    if vals.numel() != keys.numel() or vals.element_size() != 4:
+        raise ValueError("vals must hold n 32-bit payloads")
+    if vals.device != keys.device:
+        raise ValueError("vals must be on the keys' device")
+
+
+def _segments(offsets: torch.Tensor | None, keys: torch.Tensor) -> int:
+    """Segment count of ``offsets`` (int64, count + 1 entries, on the keys' device); 1 without."""
+    if offsets is None:
+        return 1
+    if offsets.dtype != torch.int64:
+        raise TypeError("offsets must be int64")
+    if offsets.device != keys.device:
+        raise ValueError("offsets must be on the keys' device")
+    return offsets.numel() - 1
+
+
+def _ws_bytes(workspace: torch.Tensor, keys: torch.Tensor) -> int:
+    if workspace.device != keys.device:
+        raise ValueError("workspace must be on the keys' device")
+    return workspace.numel() * workspace.element_size()
+
+
 def ps_workspace_size(key_type: int, has_vals: bool, n: int, segmented: bool = False,
                       tree: int = PS_TREE_POWERSORT) -> int:
     if tree == PS_TREE_POWERSORT:
@@ -164,12 +204,11 @@ def _workspace(nbytes: int, device) -> torch.Tensor:
 def ps_sort_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
                key_type: int | None = None, stream=None) -> None:
     """Stable in-place sort of ``keys`` (and ``vals``) with a caller-provided workspace tensor."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
-        raise ValueError("vals must hold n 32-bit payloads")
+    _check_vals(vals, keys)
     _check(load().ps_sort_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
-                             _dev_ptr(workspace, "workspace"), workspace.numel(),
+                             _dev_ptr(workspace, "workspace"), _ws_bytes(workspace, keys),
                              _stream_ptr(stream, keys.device)), "ps_sort_ws")
 
 
@@ -178,10 +217,9 @@ def ps_sort(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: int 
     """Stable in-place powersort of a CUDA tensor of keys (int32 / uint32 / uint64 / float32 in
     IEEE totalOrder), carrying an optional 32-bit payload.  The workspace comes from PyTorch's
     caching allocator, or from the library's own stream-ordered pool when ``pool``."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
-        raise ValueError("vals must hold n 32-bit payloads")
+    _check_vals(vals, keys)
     sp = _stream_ptr(stream, keys.device)
     if pool:
         _check(load().ps_sort(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n, sp), "ps_sort")
@@ -196,21 +234,19 @@ def ps_sort_tree_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: to
                     tree: int = PS_TREE_PEEKSORT, offsets: torch.Tensor | None = None,
                     key_type: int | None = None, stream=None) -> None:
     """ps_sort_ws / ps_sort_segmented_ws with the merge tree chosen by ``tree``."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
-        raise ValueError("vals must hold n 32-bit payloads")
-    seg = offsets is not None
+    _check_vals(vals, keys)
+    count = _segments(offsets, keys)
     _check(load().ps_sort_tree_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
-                                  _dev_ptr(offsets, "offsets") if seg else None,
-                                  (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(workspace, "workspace"),
-                                  workspace.numel(), _stream_ptr(stream, keys.device)), "ps_sort_tree_ws")
+                                  _dev_ptr(offsets, "offsets"), count, int(tree), _dev_ptr(workspace, "workspace"),
+                                  _ws_bytes(workspace, keys), _stream_ptr(stream, keys.device)), "ps_sort_tree_ws")
 
 
 def ps_sort_tree(keys: torch.Tensor, vals: torch.Tensor | None = None, tree: int = PS_TREE_PEEKSORT,
                  offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> torch.Tensor:
     """In-place stable sort with the merge tree chosen by ``tree`` (workspace from PyTorch)."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     ws = _workspace(ps_workspace_size(kt, vals is not None, keys.numel(), offsets is not None, tree), keys.device)
     ps_sort_tree_ws(keys, vals, ws, tree, offsets, kt, stream)
     return keys
@@ -219,22 +255,20 @@ def ps_sort_tree(keys: torch.Tensor, vals: torch.Tensor | None = None, tree: int
 def ps_sort_minrun_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor, min_run: int,
                       offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> None:
     """ps_sort_ws / ps_sort_segmented_ws with runs extended to ``min_run`` elements (Sec. 5.1)."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
-        raise ValueError("vals must hold n 32-bit payloads")
-    seg = offsets is not None
+    _check_vals(vals, keys)
+    count = _segments(offsets, keys)
     _check(load().ps_sort_minrun_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
-                                    _dev_ptr(offsets, "offsets") if seg else None,
-                                    (offsets.numel() - 1) if seg else 1, int(min_run),
-                                    _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                    _dev_ptr(offsets, "offsets"), count, int(min_run),
+                                    _dev_ptr(workspace, "workspace"), _ws_bytes(workspace, keys),
                                     _stream_ptr(stream, keys.device)), "ps_sort_minrun_ws")
 
 
 def ps_sort_minrun(keys: torch.Tensor, vals: torch.Tensor | None = None, min_run: int = 24,
                    offsets: torch.Tensor | None = None, key_type: int | None = None, stream=None) -> torch.Tensor:
     """In-place stable sort with runs extended to ``min_run`` elements (workspace from PyTorch)."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     ws = _workspace(ps_workspace_size(kt, vals is not None, keys.numel(), offsets is not None), keys.device)
     ps_sort_minrun_ws(keys, vals, ws, min_run, offsets, kt, stream)
     return keys
@@ -243,11 +277,12 @@ def ps_sort_minrun(keys: torch.Tensor, vals: torch.Tensor | None = None, min_run
 def ps_sort_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: torch.Tensor,
                       key_type: int | None = None, stream=None) -> torch.Tensor:
     """Sort every segment [offsets[k], offsets[k+1]) on its own (offsets: CUDA int64, count+1)."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if offsets.dtype != torch.int64:
-        raise TypeError("offsets must be int64")
-    count = offsets.numel() - 1
+    _check_vals(vals, keys)
+    if offsets is None:
+        raise ValueError("offsets are required")
+    count = _segments(offsets, keys)
     ws = _workspace(ps_workspace_size(kt, vals is not None, n, True), keys.device)
     _check(load().ps_sort_segmented_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
                                        _dev_ptr(offsets, "offsets"), count, _dev_ptr(ws, "workspace"),
@@ -257,10 +292,15 @@ def ps_sort_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: to
 
 
 def ps_sort_segmented_ws(keys, vals, offsets, workspace, key_type=None, stream=None) -> None:
-    kt = key_type_of(keys) if key_type is None else key_type
+    """ps_sort_segmented with a caller-provided workspace tensor."""
+    kt = _key_type(keys, key_type)
+    _check_vals(vals, keys)
+    if offsets is None:
+        raise ValueError("offsets are required")
+    count = _segments(offsets, keys)
     _check(load().ps_sort_segmented_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
-                                       _dev_ptr(offsets, "offsets"), offsets.numel() - 1,
-                                       _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                       _dev_ptr(offsets, "offsets"), count,
+                                       _dev_ptr(workspace, "workspace"), _ws_bytes(workspace, keys),
                                        _stream_ptr(stream, keys.device)), "ps_sort_segmented_ws")
 
 
@@ -279,9 +319,10 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
     untouched); returns numpy arrays: starts, desc, power, leaf_depth, node_left, node_right,
     node_depth, and runs, cost.  With ``min_run`` > 1 the runs are extended to that length
     (powersort tree only) and desc carries bit 1 for extended runs."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
     seg = offsets is not None
+    count = _segments(offsets, keys)
     ws = _workspace(ps_workspace_size(kt, False, n, seg, tree), keys.device)
     cap = n + 2
     out = {"starts": np.empty(cap, np.int32), "desc": np.empty(cap, np.uint8), "power": np.empty(cap, np.uint8),
@@ -296,8 +337,7 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
         fn, sel = load().ps_analyze_minrun, int(min_run)
     else:
         fn, sel = load().ps_analyze_tree, int(tree)
-    _check(fn(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets") if seg else None,
-              (offsets.numel() - 1) if seg else 1, sel, _dev_ptr(ws, "workspace"),
+    _check(fn(kt, _dev_ptr(keys, "keys"), n, _dev_ptr(offsets, "offsets"), count, sel, _dev_ptr(ws, "workspace"),
               ws.numel(), ctypes.byref(runs), ctypes.byref(cost), p["starts"], p["desc"],
               p["power"], p["leaf_depth"], p["node_left"], p["node_right"], p["node_depth"],
               _stream_ptr(stream, keys.device)), "ps_analyze")
@@ -310,7 +350,7 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
 
 
 def ps_sort_stats(keys: torch.Tensor, key_type: int | None = None, stream=None) -> dict:
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     st = _Stats()
     _check(load().ps_sort_stats(kt, _dev_ptr(keys, "keys"), keys.numel(), ctypes.byref(st),
                                 _stream_ptr(stream, keys.device)), "ps_sort_stats")
@@ -339,9 +379,19 @@ def ps_sort_host(keys_in: np.ndarray, vals_in: np.ndarray | None, keys_out: np.n
                  vals_out: np.ndarray | None, key_type: int, stream=None) -> None:
     """Sort host arrays through the GPU (copies in, sorts, copies out; synchronizes)."""
     n = keys_in.size
-    for a in (keys_in, vals_in, keys_out, vals_out):
-        if a is not None and not a.flags["C_CONTIGUOUS"]:
+    if key_type not in _KEY_BYTES:
+        raise ValueError(f"unknown key type {key_type}")
+    if (vals_in is None) != (vals_out is None):
+        raise ValueError("give both vals_in and vals_out, or neither")
+    for a, width in ((keys_in, _KEY_BYTES[key_type]), (keys_out, _KEY_BYTES[key_type]), (vals_in, 4), (vals_out, 4)):
+        if a is None:
+            continue
+        if not a.flags["C_CONTIGUOUS"]:
             raise ValueError("host arrays must be contiguous")
+        if a.size != n or a.itemsize != width:
+            raise ValueError(f"host arrays must hold n = {n} elements of {width} bytes (got {a.size} of {a.itemsize})")
+    if not keys_out.flags["WRITEABLE"] or (vals_out is not None and not vals_out.flags["WRITEABLE"]):
+        raise ValueError("output arrays must be writeable")
     sp = _stream_ptr(stream, torch.device("cuda", torch.cuda.current_device()))
     ptr = (lambda a: None if a is None else ctypes.c_void_p(a.ctypes.data))
     _check(load().ps_sort_host(key_type, ptr(keys_in), ptr(vals_in), ptr(keys_out), ptr(vals_out), n, sp),
@@ -379,10 +429,19 @@ def ps_sort_host_ws(key_type: int, keys_in: int, vals_in: int | None, keys_out: 
     """Queue copy-in, sort and copy-out of host arrays (raw host pointers, pinned for asynchrony)
     through caller-owned device buffers on ``stream``; synchronize the stream before reading the
     output."""
+    if key_type not in _KEY_BYTES:
+        raise ValueError(f"unknown key type {key_type}")
+    if dev_keys.numel() < n or dev_keys.element_size() != _KEY_BYTES[key_type]:
+        raise ValueError(f"dev_keys must hold at least n = {n} keys of {_KEY_BYTES[key_type]} bytes")
+    if (not vals_in) != (dev_vals is None) or (not vals_out) != (dev_vals is None):
+        raise ValueError("vals_in, vals_out and dev_vals go together")
+    if dev_vals is not None and (dev_vals.numel() < n or dev_vals.element_size() != 4
+                                 or dev_vals.device != dev_keys.device):
+        raise ValueError(f"dev_vals must hold at least n = {n} 32-bit payloads on the keys' device")
     _check(load().ps_sort_host_ws(key_type, ctypes.c_void_p(keys_in), ctypes.c_void_p(vals_in) if vals_in else None,
                                   ctypes.c_void_p(keys_out), ctypes.c_void_p(vals_out) if vals_out else None, n,
                                   _dev_ptr(dev_keys, "dev_keys"), _dev_ptr(dev_vals, "dev_vals"),
-                                  _dev_ptr(workspace, "workspace"), workspace.numel(),
+                                  _dev_ptr(workspace, "workspace"), _ws_bytes(workspace, dev_keys),
                                   _stream_ptr(stream, dev_keys.device)), "ps_sort_host_ws")
 
 
@@ -391,15 +450,13 @@ def ps_sort_async_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: t
                      key_type: int | None = None, stream=None) -> None:
     """Device-driven sort (no host round trip; capturable into a CUDA graph).  Device-side
     errors are reported by ``ps_stream_status``."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     n = keys.numel()
-    if vals is not None and (vals.numel() != n or vals.element_size() != 4):
-        raise ValueError("vals must hold n 32-bit payloads")
-    seg = offsets is not None
+    _check_vals(vals, keys)
+    count = _segments(offsets, keys)
     _check(load().ps_sort_async_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
-                                   _dev_ptr(offsets, "offsets") if seg else None,
-                                   (offsets.numel() - 1) if seg else 1, int(tree), _dev_ptr(workspace, "workspace"),
-                                   workspace.numel(), _stream_ptr(stream, keys.device)), "ps_sort_async_ws")
+                                   _dev_ptr(offsets, "offsets"), count, int(tree), _dev_ptr(workspace, "workspace"),
+                                   _ws_bytes(workspace, keys), _stream_ptr(stream, keys.device)), "ps_sort_async_ws")
 
 
 class _Tune(ctypes.Structure):
@@ -412,7 +469,7 @@ def ps_autotune(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: 
                 stream=None) -> dict:
     """Time every level-pass configuration on copies of ``keys``/``vals`` (unchanged) and keep the
     fastest for this key type and payload choice; returns the choice and all timings."""
-    kt = key_type_of(keys) if key_type is None else key_type
+    kt = _key_type(keys, key_type)
     out = _Tune()
     _check(load().ps_autotune(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(), ctypes.byref(out),
                               _stream_ptr(stream, keys.device)), "ps_autotune")

@@ -117,3 +117,39 @@ def test_tuning_table_without_gpu(lib):
         ps.ps_tune_set(0, True, 10, 2)  # not a configuration the library carries
     ps.ps_tune_set(0, True, 0, 0)
     assert ps.ps_tune_get(0, True) == (8, 2)
+
+
+def test_binding_rejects_mismatched_buffers_without_gpu(lib):
+    """The Python binding checks what the C ABI cannot see behind its pointers (key width against
+    the key type, payload and offsets sizes, dtypes and devices) before anything is launched."""
+    import torch
+
+    import paper_1805_04154_gb300 as ps
+    k32 = torch.zeros(8, dtype=torch.int32)
+    ws = torch.zeros(256, dtype=torch.uint8)
+    with pytest.raises(ValueError, match="8-byte keys"):
+        ps.ps_sort_ws(k32, None, ws, key_type=ps.PS_KEY_U64)
+    with pytest.raises(ValueError, match="unknown key type"):
+        ps.ps_sort_ws(k32, None, ws, key_type=7)
+    with pytest.raises(ValueError, match="32-bit payloads"):
+        ps.ps_sort_ws(k32, torch.zeros(7, dtype=torch.int32), ws)
+    with pytest.raises(ValueError, match="32-bit payloads"):
+        ps.ps_sort_async_ws(k32, torch.zeros(8, dtype=torch.int64), ws)
+    with pytest.raises(TypeError, match="int64"):
+        ps.ps_sort_tree_ws(k32, None, ws, offsets=torch.tensor([0, 8], dtype=torch.int32))
+    with pytest.raises(TypeError, match="int64"):
+        ps.ps_sort_segmented_ws(k32, None, torch.tensor([0, 8], dtype=torch.int32), ws)
+    with pytest.raises(ValueError, match="offsets are required"):
+        ps.ps_sort_segmented(k32, None, None)
+    with pytest.raises(ValueError, match="32-bit payloads"):
+        ps.ps_sort_segmented(k32, torch.zeros(9, dtype=torch.int32), torch.tensor([0, 8]))
+    # host arrays: sizes and widths against n and the key type
+    a = np.zeros(8, np.int32)
+    with pytest.raises(ValueError, match="8 elements of 4 bytes"):
+        ps.ps_sort_host(a, None, np.zeros(7, np.int32), None, ps.PS_KEY_I32)
+    with pytest.raises(ValueError, match="of 8 bytes"):
+        ps.ps_sort_host(a, None, np.zeros(8, np.int32), None, ps.PS_KEY_U64)
+    with pytest.raises(ValueError, match="neither"):
+        ps.ps_sort_host(a, np.zeros(8, np.uint32), np.zeros(8, np.int32), None, ps.PS_KEY_I32)
+    with pytest.raises(ValueError, match="dev_keys"):
+        ps.ps_sort_host_ws(ps.PS_KEY_I32, 1, None, 1, None, 16, k32, None, ws)
