@@ -72,6 +72,8 @@ class SortServer:
     def __init__(self, key_type: int, budget_bytes: int = 64 << 30, max_batch_keys: int = 1 << 25,
                  slots: int = 3, device: int | None = None, with_vals: bool = True):
         load()
+        if key_type not in _KEY_BYTES:
+            raise ValueError(f"unknown key type {key_type}")
         self.kt = key_type
         self.kb = _KEY_BYTES[key_type]
         self.kdt = {4: torch.int32, 8: torch.int64}[self.kb]
@@ -119,6 +121,10 @@ class SortServer:
             raise ValueError("this server carries a 32-bit payload per key")
         if keys.numel() > self.cap:
             raise ValueError(f"request of {keys.numel()} keys exceeds the arena slot ({self.cap} keys)")
+        for t, width, name in ((out_keys, self.kb, "out_keys"), (out_vals if self.with_vals else None, 4, "out_vals")):
+            if t is not None and (t.device.type != "cpu" or not t.is_contiguous() or t.numel() != keys.numel()
+                                  or t.element_size() != width):
+                raise ValueError(f"{name} must be a contiguous CPU tensor shaped like the request")
         r = Request(0, keys, vals if self.with_vals else None,
                     keys if out_keys is None else out_keys,
                     (vals if out_vals is None else out_vals) if self.with_vals else None, t)
