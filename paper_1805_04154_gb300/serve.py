@@ -226,9 +226,14 @@ class SortServer:
                 if not self._busy:
                     return
                 slot = self._busy[0]
-            slot.done_event.synchronize()
+            err = None
+            try:
+                slot.done_event.synchronize()
+            except Exception as e:  # a CUDA error: report it on the batch's requests, keep serving
+                err = str(e)
             t = time.perf_counter()
             for r in slot.reqs:
+                r.error = err
                 r.t_done = t
                 r.done.set()
             with self._cv:
