@@ -51,11 +51,11 @@ class HostSortPipeline:
         if (vals_in is None) != (not self.with_vals) or (vals_out is None) != (vals_in is None):
             raise ValueError("payloads must be given exactly when the pipeline was built with_vals")
         kb = self._sets[0][0].element_size()
-        for t, width, name in ((keys_in, kb, "keys_in"), (keys_out, kb, "keys_out"), (vals_in, 4, "vals_in"),
-                               (vals_out, 4, "vals_out")):
-            if t is None:
+        for buf, width, name in ((keys_in, kb, "keys_in"), (keys_out, kb, "keys_out"), (vals_in, 4, "vals_in"),
+                                 (vals_out, 4, "vals_out")):
+            if buf is None:
                 continue
-            if t.is_cuda or not t.is_contiguous() or t.numel() != n or t.element_size() != width:
+            if buf.is_cuda or not buf.is_contiguous() or buf.numel() != n or buf.element_size() != width:
                 raise ValueError(f"{name} must be a contiguous host tensor of n = {n} elements of {width} bytes")
         k, v, w, st = self._sets[self._next]
         self._next = (self._next + 1) % len(self._sets)

@@ -114,20 +114,20 @@ class SortServer:
         """Queue one sort of host tensors (pinned memory gives asynchronous copies).  The result
         goes to out_keys/out_vals, or back into keys/vals when those are not given.  Returns a
         Request whose ``done`` event is set when the result is in host memory."""
-        t = time.perf_counter()
+        t_submit = time.perf_counter()
         if keys.device.type != "cpu" or not keys.is_contiguous() or keys.element_size() != self.kb:
             raise TypeError("keys must be a contiguous CPU tensor of the server's key width")
         if self.with_vals and (vals is None or vals.numel() != keys.numel() or vals.element_size() != 4):
             raise ValueError("this server carries a 32-bit payload per key")
         if keys.numel() > self.cap:
             raise ValueError(f"request of {keys.numel()} keys exceeds the arena slot ({self.cap} keys)")
-        for t, width, name in ((out_keys, self.kb, "out_keys"), (out_vals if self.with_vals else None, 4, "out_vals")):
-            if t is not None and (t.device.type != "cpu" or not t.is_contiguous() or t.numel() != keys.numel()
-                                  or t.element_size() != width):
+        for buf, width, name in ((out_keys, self.kb, "out_keys"), (out_vals if self.with_vals else None, 4, "out_vals")):
+            if buf is not None and (buf.device.type != "cpu" or not buf.is_contiguous()
+                                    or buf.numel() != keys.numel() or buf.element_size() != width):
                 raise ValueError(f"{name} must be a contiguous CPU tensor shaped like the request")
         r = Request(0, keys, vals if self.with_vals else None,
                     keys if out_keys is None else out_keys,
-                    (vals if out_vals is None else out_vals) if self.with_vals else None, t)
+                    (vals if out_vals is None else out_vals) if self.with_vals else None, t_submit)
         with self._cv:
             r.rid = self._next_id
             self._next_id += 1
