@@ -128,6 +128,10 @@ struct ThreadRuns {
       }
       if (kDetectItems < n - p0) L |= (uint64_t)(K::ord(prev) <= K::ord(keys[p0 + kDetectItems])) << kDetectItems;
     }
+    forced_starts(offsets, count);
+  }
+  // F from position 0 and the segment offsets
+  __device__ __forceinline__ void forced_starts(const int64_t* __restrict__ offsets, int32_t count) {
     if (p0 == 0) F |= 1ull;
     if (offsets != nullptr) {
       // every offsets value in [p0, p0 + kDetectItems] marks a forced start
@@ -139,6 +143,59 @@ struct ThreadRuns {
         ++k;
       }
     }
+  }
+  // The same view for 4-byte keys, the warp's 32 x 32 keys staged through shared memory: each
+  // lane issues eight 16-byte cp.async copies at lane-consecutive addresses (coalesced, no
+  // registers held while they are in flight), then reads its own 32 keys back.  Chunk c of lane
+  // l's 128-byte row is stored at index c ^ (l & 7) of the row, so the copies of a quarter warp
+  // (one row) and the row reads of a quarter warp (eight rows, one chunk index each) both cover
+  // eight distinct 16-byte bank groups.  The pairs into the lane's first position and out of its
+  // last one use the neighbouring lanes' keys.  A warp whose keys (with the look-ahead) are not
+  // wholly inside the array, or whose keys are not 16-byte aligned, takes load().
+  __device__ __forceinline__ void load_staged(const T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+                                              int32_t count, int32_t tile, int tid, uint4* __restrict__ stage) {
+    static_assert(sizeof(T) == 4 && kDetectItems == 32, "a lane row is 8 chunks of 4 keys");
+    constexpr int kWarpKeys = 32 * kDetectItems;
+    const int lane = tid & 31;
+    const int32_t wp0 = tile * kDetectTile + (tid - lane) * kDetectItems;
+    if (!(kWarpKeys < n - wp0 && ((uintptr_t)keys & 15u) == 0)) {  // uniform over the warp
+      load(keys, n, offsets, count, tile, tid);
+      return;
+    }
+    const uint4* __restrict__ src = reinterpret_cast<const uint4*>(keys + wp0);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int g = j * 32 + lane, row = g >> 3, c = g & 7;  // chunk g of the warp's 256
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(stage + row * 8 + (c ^ (row & 7)))),
+                   "l"(src + g)
+                   : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    p0 = wp0 + lane * kDetectItems;
+    nvalid = kDetectItems;
+    valid = (1ull << kDetectItems) - 1ull;
+    L = 0;
+    F = 0;
+    T first = 0, last = 0;
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const uint4 w = stage[lane * 8 + (v ^ (lane & 7))];
+      const T wt[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (v == 0 && u == 0) first = wt[0];
+        else L |= (uint64_t)(K::ord(last) <= K::ord(wt[u])) << (v * 4 + u);
+        last = wt[u];
+      }
+    }
+    T before = __shfl_up_sync(0xffffffffu, last, 1);
+    T after = __shfl_down_sync(0xffffffffu, first, 1);
+    if (lane == 0) before = (p0 > 0) ? keys[p0 - 1] : (T)0;
+    if (lane == 31) after = keys[p0 + kDetectItems];  // p0 + 32 = wp0 + kWarpKeys < n
+    L |= (uint64_t)(K::ord(before) <= K::ord(first));
+    L |= (uint64_t)(K::ord(last) <= K::ord(after)) << kDetectItems;
+    forced_starts(offsets, count);
   }
   // rebuild the view from the pair / forced-start masks the reduce pass saved
   __device__ __forceinline__ void restore(int32_t n, int32_t tile, int tid, uint64_t l, uint64_t f) {
@@ -205,9 +262,12 @@ detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const in
                      int32_t count, uint64_t* __restrict__ tile_agg, uint64_t* __restrict__ thr_L,
                      uint64_t* __restrict__ thr_F, uint32_t* __restrict__ thr_fn) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
+  constexpr bool kStaged = sizeof(typename K::T) == 4;
+  __shared__ uint4 stage[kStaged ? kDetectThreads / 32 * 256 : 1];  // 4 KB of keys per warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ThreadRuns<K> tr;
-  tr.load(keys, n, offsets, count, blockIdx.x, tid);
+  if constexpr (kStaged) tr.load_staged(keys, n, offsets, count, blockIdx.x, tid, stage + warp * 256);
+  else tr.load(keys, n, offsets, count, blockIdx.x, tid);
   Fn incl = tr.aggregate();
   // the emit pass replays the runs from these instead of reading the keys again
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
