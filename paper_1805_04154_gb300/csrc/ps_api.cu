@@ -34,12 +34,8 @@ const KeyLaunch* launch_for(int kt) {
 
 int key_bytes(int kt) { return kt == PS_KEY_U64 ? 8 : 4; }
 
-// Chunk-boundary slots of one fused pass: per node floor(size / kChunkSpan) + 2, for at most
-// `cap` nodes (those larger than the subtree limit).
-size_t chunk_capacity(int64_t n, size_t cap) { return (size_t)n / kChunkSpan + 2 * cap + 64; }
-
 // Carve the workspace into the per-call arrays.  With base == nullptr only the size is computed.
-size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented, bool fused, int tree = 0) {
+size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented, int tree = 0) {
   size_t cur = 0;
   auto take = [&](size_t bytes) -> void* {
     cur = (cur + 255) & ~(size_t)255;
@@ -80,13 +76,6 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.sub_lim = sub_tile((int)kb);
   c.small_tasks = (int32_t*)take(N * 4);
   const size_t cap = (size_t)n / (size_t)(c.sub_lim + 1) + 2;
-  if (fused) {
-    c.lsplit = (int32_t*)take(N * 4);
-    c.rsplit = (int32_t*)take(N * 4);
-    c.chunk_tab = (int4*)take(chunk_capacity(n, cap) * sizeof(int4));
-    c.item_ext = (int4*)take(cap * sizeof(int4));
-  }
-  c.fused = fused;
   c.tree = tree;
   if (tree == PS_TREE_PEEKSORT) {
     // ranges of one tree level: disjoint, each holding >= 2 runs, so at most (r + 1) / 2
@@ -260,19 +249,6 @@ void apply_pass_config(Ctx& c, int kt, bool vals) {
   c.merge_tile = c.pass_ipt * kMergeThreads;
 }
 
-// Binary passes (one tree level per HBM pass) unless PS_FUSED=1 selects fused passes (two tree
-// levels per HBM pass).  Measured on GB300 at n = 1e8, the fused pass moves half the bytes but
-// executes twice the merge work per byte and is compute-bound: 4.9 ms against 3.9 ms for the
-// binary passes of the same sort, so binary passes are the default.
-bool fused_setting() {
-  static int v = -1;
-  if (v < 0) {
-    const char* e = std::getenv("PS_FUSED");
-    v = (e && e[0] == '1') ? 1 : 0;
-  }
-  return v != 0;
-}
-
 ps_status cuda_status(cudaError_t e) {
   if (e == cudaSuccess) return PS_OK;
   if (e == cudaErrorMemoryAllocation) return PS_ERR_OUT_OF_MEMORY;
@@ -324,6 +300,23 @@ ps_status read_plan_header(const Ctx& c, int dev, PlanHeader& h) {
   return PS_OK;
 }
 
+// The counts the merge launches are sized with must fit the plan's arrays: subtree tasks
+// (<= n + 2 slots), large leaves (<= level_cap items, <= n tiles) and, per depth, level-pass
+// items (<= level_cap) and tiles (a node of size s spans at most s / tile + 2 tiles).  A plan
+// that breaks one of them is reported instead of launched.
+bool plan_counts_ok(const Ctx& c, const PlanHeader& h, int64_t n) {
+  if (h.runs < 1 || h.runs > n) return false;
+  if ((uint64_t)h.n_small > (uint64_t)n + 2) return false;
+  if ((h.leaf_ctr >> 32) > (uint64_t)c.level_cap || (h.leaf_ctr & 0xffffffffull) > (uint64_t)n) return false;
+  for (int d = 0; d < kMaxLevels; ++d) {
+    const uint64_t items = h.level_ctr[d] >> 32, tiles = h.level_ctr[d] & 0xffffffffull;
+    if (tiles == 0) continue;
+    if (items > (uint64_t)c.level_cap) return false;
+    if (tiles > (uint64_t)n / (uint64_t)c.merge_tile + 2ull * items + 1) return false;
+  }
+  return true;
+}
+
 // The whole pipeline.  With `an` set, stops after planning and reports the plan instead.
 ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
               bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, AnalyzeOut* an, int tree = 0,
@@ -347,7 +340,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     return PS_OK;
   }
   Ctx c;
-  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, fused_setting(), tree);
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, tree);
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
   int dev = 0;
   PS_TRY(cudaGetDevice(&dev));
@@ -391,10 +384,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
   const int32_t r = h.runs;
-  if (r < 1 || r > n) return PS_ERR_INTERNAL;
-  // the counts the merge launches are sized with must fit the plan's arrays
-  if ((uint64_t)h.n_small > (uint64_t)n + 2) return PS_ERR_INTERNAL;
-  if ((h.leaf_ctr >> 32) > (uint64_t)c.level_cap || (h.leaf_ctr & 0xffffffffull) > (uint64_t)n) return PS_ERR_INTERNAL;
+  if (!plan_counts_ok(c, h, n)) return PS_ERR_INTERNAL;
 
   if (an) {
     if (an->runs) *an->runs = r;
@@ -441,19 +431,9 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
-    if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
-    if (!c.fused && (uint64_t)tiles > (uint64_t)n / (uint64_t)c.merge_tile + 2ull * items + 1) return PS_ERR_INTERNAL;
-    if (c.fused) {
-      // fused passes exist at even depths only; tiles counts chunk-boundary slots
-      if ((d & 1) || (uint64_t)tiles > chunk_capacity(n, (size_t)c.level_cap)) return PS_ERR_INTERNAL;
-      StageTimer t(5, s);
-      PS_TRY(kl->fused_merge(c, d, items, tiles));
-      t.done(2 * h.level_elems[d] * eb, 2);
-    } else {
-      StageTimer t(5, s);
-      PS_TRY(kl->merge(c, d, items, tiles));
-      t.done(2 * h.level_elems[d] * eb, 1);
-    }
+    StageTimer t(5, s);
+    PS_TRY(kl->merge(c, d, items, tiles));
+    t.done(2 * h.level_elems[d] * eb, 1);
   }
   return PS_OK;
 }
@@ -471,7 +451,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
   if (n <= 1) return PS_OK;
   Ctx c;
-  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, false, tree);
+  const size_t need = carve(c, (uint8_t*)ws, kt, vals != nullptr, n, segmented, tree);
   if (!ws || ws_bytes < need || ((uintptr_t)ws & 255u)) return ws ? PS_ERR_OUT_OF_MEMORY : PS_ERR_INVALID_ARG;
   int dev = 0;
   PS_TRY(cudaGetDevice(&dev));
@@ -536,7 +516,7 @@ ps_status with_pool(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   cudaMemPool_t pool = lib_pool(dev);
   if (!pool) return PS_ERR_CUDA;
   Ctx tmp;
-  const size_t bytes = carve(tmp, nullptr, kt, vals != nullptr, n, segmented, fused_setting());
+  const size_t bytes = carve(tmp, nullptr, kt, vals != nullptr, n, segmented);
   void* ws = nullptr;
   cudaError_t e = cudaMallocFromPoolAsync(&ws, bytes, pool, s);
   if (e != cudaSuccess) return PS_ERR_OUT_OF_MEMORY;
@@ -605,7 +585,7 @@ extern "C" {
 size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented) {
   if (!launch_for(key_type) || n < 0) return 0;
   Ctx c;
-  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0, fused_setting());
+  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0);
 }
 
 ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,
@@ -706,7 +686,7 @@ ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int6
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals ? up((size_t)n * 4 + 16) : 0;
   Ctx tmp;
-  const size_t wbytes = carve(tmp, nullptr, key_type, vals != nullptr, n, false, fused_setting());
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals != nullptr, n, false);
   uint8_t* base = nullptr;
   if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
     return PS_ERR_OUT_OF_MEMORY;
@@ -774,7 +754,7 @@ ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, 
 size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segmented, int tree) {
   if (!launch_for(key_type) || n < 0 || (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT)) return 0;
   Ctx c;
-  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0, fused_setting(), tree);
+  return carve(c, nullptr, key_type, has_vals != 0, n, segmented != 0, tree);
 }
 
 ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
@@ -894,7 +874,7 @@ ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_i
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals_in ? up((size_t)n * 4 + 16) : 0;
   Ctx tmp;
-  const size_t wbytes = carve(tmp, nullptr, key_type, vals_in != nullptr, n, false, fused_setting());
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals_in != nullptr, n, false);
   uint8_t* base = nullptr;
   if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
     return PS_ERR_OUT_OF_MEMORY;
@@ -1025,7 +1005,7 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   uint8_t* scratch = noalloc_scratch(dev);
   if (!scratch) return PS_ERR_CUDA;
   Ctx c;
-  const size_t need = carve(c, scratch, kt, vals != nullptr, n, false, false);
+  const size_t need = carve(c, scratch, kt, vals != nullptr, n, false);
   if (need + 256 > kNoAllocScratchBytes) return PS_ERR_INTERNAL;
   c.stream = s;
   c.kt = kt;
@@ -1037,26 +1017,28 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = (uint32_t*)(scratch + kNoAllocScratchBytes - 256);  // this entry's own status word
+  apply_pass_config(c, kt, vals != nullptr);  // the level-pass configuration every other sort uses
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
   PS_TRY(cudaMemsetAsync(c.lib_status, 0, 4, s));
   PS_TRY(kl->detect(c));
   PS_TRY(launch_meta_stages(c));
-  g_launches += 11;
+  g_launches += 3 + (uint64_t)meta_launches(c);
   PlanHeader h;
   PS_TRY(cudaMemcpyAsync(&h, c.hdr, sizeof(PlanHeader), cudaMemcpyDeviceToHost, s));
   PS_TRY(cudaStreamSynchronize(s));
   if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
-  if (h.runs < 1 || h.runs > n) return PS_ERR_INTERNAL;
+  // the same bounds on the plan's counts as every other entry point: a plan that broke them
+  // would make the launches below write past their regions of the shared scratch array
+  if (!plan_counts_ok(c, h, n)) return PS_ERR_INTERNAL;
   PS_TRY(kl->small(c, h.n_small));
   PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), (uint32_t)(h.leaf_ctr & 0xffffffffull)));
   g_launches += (h.n_small ? 1 : 0) + ((h.leaf_ctr & 0xffffffffull) ? 1 : 0);
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
     if (tiles == 0) continue;
-    if ((int64_t)items > c.level_cap) return PS_ERR_INTERNAL;
     PS_TRY(kl->merge(c, d, items, tiles));
     g_launches += 1;
   }

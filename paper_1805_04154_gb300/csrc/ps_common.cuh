@@ -36,19 +36,10 @@ constexpr int kMergeThreads = 256;
 constexpr int kMergeItems = 12;
 constexpr int kMergeTile = kMergeThreads * kMergeItems;  // 3072
 
-// Stage 4, fused passes: one HBM pass merges a node of even depth straight from the up to four
-// ranges below it (its children, or its grandchildren under a child of odd depth).  Chunk
-// boundaries are taken every kChunkSpan elements of each range, so a chunk draws fewer than
-// kChunkSpan + 1 elements from each range; a tile groups whole chunks up to kFusedTile outputs.
-constexpr int kChunkSpan = 512;
-constexpr int kFusedTile = kMergeTile - 2 * kMergeItems;  // room for two ragged phase-1 merges and
-                                                         // 16-byte aligned output ranges
-
 // Buffer (0 = the caller's arrays, 1 = scratch) that holds the sorted output of a materialised
-// node or leaf at depth d.  Binary passes: a node at depth d writes d mod 2.  Fused passes
-// write only at even depths 2e (buffer e mod 2); nodes and leaves at depth 2e-1 or 2e are read
-// by the pass at depth 2e-2, so they sit in buffer e mod 2 as well: ceil(d / 2) mod 2.
-__host__ __device__ constexpr int out_buffer(int d, bool fused) { return fused ? (((d + 1) >> 1) & 1) : (d & 1); }
+// node or leaf at depth d: a node at depth d writes buffer d mod 2 and reads its children from
+// buffer (d + 1) mod 2, so the root lands in the caller's arrays.
+__host__ __device__ constexpr int out_buffer(int d) { return d & 1; }
 
 // Stage 4 (whole small subtrees in shared memory): a tree node whose range holds at most
 // sub_tile(key size) elements is merged completely inside one CTA.

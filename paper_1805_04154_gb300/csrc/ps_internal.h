@@ -55,15 +55,10 @@ struct Ctx {
   int pass_stages = 2;          // shared-memory stages of the level-pass ring
   int pass_ipt = kMergeItems;   // outputs per consumer thread of a level pass
   int32_t merge_tile = kMergeTile;  // outputs per level-pass tile (pass_ipt x kMergeThreads)
-  bool fused = false;           // fused passes (two tree levels per HBM pass) or binary passes
   int tree = 0;                 // merge tree: 0 powersort (Alg. 2), 1 peeksort (Alg. 1)
   int2* peek_front[2] = {nullptr, nullptr};  // peeksort: run ranges of one tree level
   uint32_t* peek_count = nullptr;            // peeksort: ranges per level [kMaxLevels + 1]
   int32_t peek_front_cap = 0;
-  int32_t* lsplit = nullptr;    // fused: split position of a node's left child of odd depth
-  int32_t* rsplit = nullptr;    //        ... and of its right child
-  int4* chunk_tab = nullptr;    // fused: chunk boundaries of the current pass (c1, c2, c3, c4)
-  int4* item_ext = nullptr;     // fused: per item of the current pass (s1, s2, samples, 0)
   int32_t* small_tasks = nullptr;
   int32_t* leaf_items = nullptr;
   uint32_t* leaf_tile_off = nullptr;
@@ -82,7 +77,6 @@ struct KeyLaunch {
   cudaError_t (*small)(const Ctx&, uint32_t ntasks);
   cudaError_t (*place)(const Ctx&, uint32_t nitems, uint32_t ntiles);
   cudaError_t (*merge)(const Ctx&, int depth, uint32_t nitems, uint32_t ntiles);
-  cudaError_t (*fused_merge)(const Ctx&, int depth, uint32_t nitems, uint32_t nslots);
 };
 extern const KeyLaunch kLaunchI32, kLaunchU32, kLaunchF32, kLaunchU64;
 

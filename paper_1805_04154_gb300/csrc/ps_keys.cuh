@@ -7,7 +7,6 @@
 #include "ps_detect.cuh"
 #include "ps_detect_minrun.cuh"
 #include "ps_internal.h"
-#include "ps_fused.cuh"
 #include "ps_level.cuh"
 #include "ps_merge.cuh"
 
@@ -73,12 +72,12 @@ struct Launch {
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     if (ntasks == kCountOnDevice)
       subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 4, kSubThreads, bytes, c.stream>>>(
-          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)(c.n + 2),
-          c.fused ? 1 : 0, c.hdr, c.lib_status);
+          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)(c.n + 2), c.hdr,
+          c.lib_status);
     else
       subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
-                                                                      c.ndepth, c.ldepth, c.small_tasks,
-                                                                      c.fused ? 1 : 0, c.hdr, c.lib_status);
+                                                                      c.ndepth, c.ldepth, c.small_tasks, c.hdr,
+                                                                      c.lib_status);
     return cudaGetLastError();
   }
   static cudaError_t small(const Ctx& c, uint32_t ntasks) {
@@ -98,7 +97,6 @@ struct Launch {
     if (ntiles == 0) return cudaSuccess;
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     const uint32_t cap = (uint32_t)c.level_cap;
-    const int fu = c.fused ? 1 : 0;
     static int occ_v = 0, occ_k = 0;
     if (occ_v == 0) {
       occ_v = resident(leaf_place_kernel<K, true>);
@@ -108,19 +106,18 @@ struct Launch {
     if (ntiles == kCountOnDevice) {
       if (c.has_vals)
         leaf_place_persistent_kernel<K, true><<<full, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                                          c.leaf_tile_off, cap, fu, c.hdr);
+                                                                          c.leaf_tile_off, cap, c.hdr);
       else
         leaf_place_persistent_kernel<K, false><<<full, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth,
-                                                                           c.leaf_items, c.leaf_tile_off, cap, fu,
-                                                                           c.hdr);
+                                                                           c.leaf_items, c.leaf_tile_off, cap, c.hdr);
     } else {
       const uint32_t grid = std::min(ntiles, full);
       if (c.has_vals)
         leaf_place_kernel<K, true><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                               c.leaf_tile_off, nitems, ntiles, fu, c.hdr);
+                                                               c.leaf_tile_off, nitems, ntiles, c.hdr);
       else
         leaf_place_kernel<K, false><<<grid, 256, 0, c.stream>>>(b, c.S, c.run_desc, c.ldepth, c.leaf_items,
-                                                                c.leaf_tile_off, nitems, ntiles, fu, c.hdr);
+                                                                c.leaf_tile_off, nitems, ntiles, c.hdr);
     }
     return cudaGetLastError();
   }
@@ -172,44 +169,7 @@ struct Launch {
     return c.has_vals ? merge_v<true>(c, depth, nitems, ntiles) : merge_v<false>(c, depth, nitems, ntiles);
   }
 
-  template <bool V, int NS>
-  static cudaError_t fused_vs(const Ctx& c, int depth, uint32_t nitems, uint32_t nslots) {
-    static int blocks_per_sm = 0;
-    static int sms = 0;
-    const size_t bytes = FusedLayout<K, V, NS>::kBytes;
-    if (blocks_per_sm == 0) {
-      cudaError_t e = cudaFuncSetAttribute(fused_pass_kernel<K, V, NS>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-      if (e != cudaSuccess) return e;
-      int dev = 0;
-      cudaGetDevice(&dev);
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, fused_pass_kernel<K, V, NS>, kPassThreads,
-                                                        bytes);
-      if (e != cudaSuccess) return e;
-      if (blocks_per_sm < 1) blocks_per_sm = 1;
-    }
-    // the pass at (even) depth d reads what depths d+1 and d+2 left in their buffer
-    const int src = out_buffer(depth + 1, true), dst = out_buffer(depth, true);
-    const size_t off = (size_t)depth * c.level_cap;
-    const uint32_t tgrid = (uint32_t)std::min<uint64_t>((nslots + 63) / 64, (uint64_t)sms * 8);  // 4 threads per slot
-    chunk_table_kernel<K><<<tgrid, 256, 0, c.stream>>>((const T*)c.k[src], c.level_items + off,
-                                                      c.level_tile_off + off, nitems, nslots, c.nodeL, c.nodeR,
-                                                      c.lsplit, c.rsplit, c.sub_lim, c.chunk_tab, c.item_ext,
-                                                      c.hdr, c.lib_status);
-    const uint32_t grid = (uint32_t)std::min<uint64_t>(nslots, (uint64_t)sms * blocks_per_sm);
-    fused_pass_kernel<K, V, NS><<<grid, kPassThreads, bytes, c.stream>>>(
-        (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.item_ext, c.level_tile_off + off,
-        nitems, nslots, c.chunk_tab, c.hdr, c.lib_status);
-    return cudaGetLastError();
-  }
-
-  static cudaError_t fused_merge(const Ctx& c, int depth, uint32_t nitems, uint32_t nslots) {
-    if (nslots == 0) return cudaSuccess;
-    return c.has_vals ? fused_vs<true, 2>(c, depth, nitems, nslots) : fused_vs<false, 2>(c, depth, nitems, nslots);
-  }
-
-  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &merge, &fused_merge}; }
+  static KeyLaunch table() { return KeyLaunch{&detect, &small, &place, &merge}; }
 };
 
 }  // namespace ps

@@ -29,7 +29,6 @@ namespace ps {
 // A ring of NS stages: the copies of the next NS-1 tiles overlap the merge of the current one.
 // All waits are bounded; a timeout posts kDevTimeout and the CTA drains its copies and exits.
 // ---------------------------------------------------------------------------------------
-constexpr int kPassThreads = kMergeThreads + 32;   // 8 consumer warps + 1 producer warp (fused passes)
 constexpr int kLevelThreads = kMergeThreads + 64;  // 8 consumer warps + issuer + searcher
 constexpr int kQueue = 8;                          // searched tiles the searcher may run ahead
 constexpr int kSearchBatch = 4;                    // tiles searched together (8 lanes each)

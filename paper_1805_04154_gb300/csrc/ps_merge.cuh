@@ -139,7 +139,7 @@ template <class K, bool V>
 __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                                              const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                                              const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-                                             const int32_t task, int fused, PlanHeader* __restrict__ hdr,
+                                             const int32_t task, PlanHeader* __restrict__ hdr,
                                              uint32_t* lib_status) {
   typedef typename K::T T;
   typedef SubElem<K> E;
@@ -403,7 +403,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
   }
 
   // 5. write-out into the buffer that holds the subtree root's output (out_buffer)
-  const bool odd = out_buffer(droot, fused != 0) == 1;  // selects, not an indexed parameter array
+  const bool odd = out_buffer(droot) == 1;  // selects, not an indexed parameter array
   T* __restrict__ ok = (T*)(odd ? buf.k[1] : buf.k[0]);
   if (V) {
     uint32_t* pay = (uint32_t*)meta;  // the node list is no longer needed
@@ -439,8 +439,8 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-               const int32_t* __restrict__ tasks, int fused, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
-  subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[blockIdx.x], fused, hdr, lib_status);
+               const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+  subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[blockIdx.x], hdr, lib_status);
 }
 
 // A persistent grid over the task count the plan left on the device (no host round trip); the
@@ -450,12 +450,12 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                           const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                           const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-                          const int32_t* __restrict__ tasks, uint32_t cap, int fused, PlanHeader* __restrict__ hdr,
+                          const int32_t* __restrict__ tasks, uint32_t cap, PlanHeader* __restrict__ hdr,
                           uint32_t* lib_status) {
   if (hdr->status & kDevBadOffsets) return;  // nothing moves when the offsets were rejected
   const uint32_t ntasks = min(hdr->n_small, cap);
   for (uint32_t tb = blockIdx.x; tb < ntasks; tb += gridDim.x) {
-    subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[tb], fused, hdr, lib_status);
+    subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[tb], hdr, lib_status);
     __syncthreads();  // the next task reuses the shared arrays
   }
 }
@@ -468,7 +468,7 @@ subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t
 // ---------------------------------------------------------------------------------------
 template <class K, bool V>
 __device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
-                                               const uint8_t* __restrict__ ldepth, int32_t i, uint32_t k, int fused) {
+                                               const uint8_t* __restrict__ ldepth, int32_t i, uint32_t k) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
   const int32_t s = S[i], e = S[i + 1];
@@ -478,7 +478,7 @@ __device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restri
   // all loads of the thread first (independent, coalesced even when reversed), then the stores
   T kx[kPer], ky[kPer];
   uint32_t vx[kPer], vy[kPer];
-  if (out_buffer(ldepth[i], fused != 0) == 1) {
+  if (out_buffer(ldepth[i]) == 1) {
     T* __restrict__ k1 = (T*)buf.k[1];
     uint32_t* __restrict__ v1 = buf.v[1];
     const int32_t q0 = s + (int32_t)k * kMergeTile + threadIdx.x;
@@ -542,7 +542,7 @@ __device__ __forceinline__ void leaf_place_range(Bufs buf, const int32_t* __rest
                                                  const uint8_t* __restrict__ run_desc,
                                                  const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                                                  const uint32_t* __restrict__ tile_off, uint32_t nitems,
-                                                 uint32_t t_begin, uint32_t t_end, int fused, int32_t runs) {
+                                                 uint32_t t_begin, uint32_t t_end, int32_t runs) {
   __shared__ int32_t s_slot;
   if (t_begin >= t_end || nitems == 0) return;  // uniform over the CTA
   if (threadIdx.x == 0) s_slot = slot_of_tile(tile_off, nitems, t_begin);
@@ -552,7 +552,7 @@ __device__ __forceinline__ void leaf_place_range(Bufs buf, const int32_t* __rest
     while (slot + 1 < (int32_t)nitems && tile_off[slot + 1] <= tile) ++slot;
     const int32_t i = items[slot];
     if (i < 0 || i >= runs) return;  // never for a consistent plan (uniform over the CTA)
-    leaf_place_one<K, V>(buf, S, run_desc, ldepth, i, tile - tile_off[slot], fused);
+    leaf_place_one<K, V>(buf, S, run_desc, ldepth, i, tile - tile_off[slot]);
   }
 }
 
@@ -561,11 +561,11 @@ template <class K, bool V>
 __global__ void __launch_bounds__(256)
 leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                   const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                  const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t ntiles, int fused,
+                  const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t ntiles,
                   const PlanHeader* __restrict__ hdr) {
   const uint32_t t0 = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
   const uint32_t t1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
-  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, fused, hdr->runs);
+  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, hdr->runs);
 }
 
 // The same over the counts the plan left on the device (no host round trip).
@@ -573,7 +573,7 @@ template <class K, bool V>
 __global__ void __launch_bounds__(256)
 leaf_place_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                              const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
-                             const uint32_t* __restrict__ tile_off, uint32_t cap, int fused,
+                             const uint32_t* __restrict__ tile_off, uint32_t cap,
                              const PlanHeader* __restrict__ hdr) {
   if (hdr->status & kDevBadOffsets) return;
   const unsigned long long v = hdr->leaf_ctr;
@@ -581,7 +581,7 @@ leaf_place_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint
   const uint32_t ntiles = (uint32_t)(v & 0xffffffffull);
   const uint32_t t0 = (uint32_t)(((uint64_t)blockIdx.x * ntiles) / gridDim.x);
   const uint32_t t1 = (uint32_t)(((uint64_t)(blockIdx.x + 1) * ntiles) / gridDim.x);
-  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, fused, hdr->runs);
+  leaf_place_range<K, V>(buf, S, run_desc, ldepth, items, tile_off, nitems, t0, t1, hdr->runs);
 }
 
 }  // namespace ps

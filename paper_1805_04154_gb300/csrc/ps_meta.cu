@@ -404,12 +404,8 @@ __global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, cons
 //  * larger leaves that must move (odd depth -> scratch buffer, or descending -> reversed) get
 //    placement tiles;
 //  * larger internal nodes are merged by HBM passes, one pass per depth.
-// Buffer parity (out_buffer): with binary passes a node at depth d writes buffer d mod 2 (0 =
-// the caller's arrays) and reads its children from buffer (d+1) mod 2, so every leaf starts in
-// buffer (depth mod 2).  With fused passes only nodes of even depth are written by HBM passes;
-// a large node of odd depth is merged inside its parent's pass (the parent learns its split
-// position through lsplit / rsplit), and everything materialised at depth d sits in buffer
-// ceil(d / 2) mod 2.
+// Buffer parity (out_buffer): a node at depth d writes buffer d mod 2 (0 = the caller's arrays)
+// and reads its children from buffer (d+1) mod 2, so every leaf starts in buffer (depth mod 2).
 // M = sum over leaves of depth x length (Sec. 2.3).
 // ---------------------------------------------------------------------------------------
 __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
@@ -418,8 +414,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
                             uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
                             int4* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
-                            int32_t level_cap, int32_t small_cap, int fused, int32_t* __restrict__ lsplit,
-                            int32_t* __restrict__ rsplit, int32_t merge_tile, PlanHeader* __restrict__ hdr) {
+                            int32_t level_cap, int32_t small_cap, int32_t merge_tile,
+                            PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   unsigned long long cost = 0;
   int32_t maxd = 0;
@@ -451,7 +447,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         const bool desc = (run_desc[x] & 1) != 0;
         if (run_desc[x] & 2) post_status(&hdr->status, nullptr, kDevInternal);  // extended runs are short
         uint32_t tiles = 0;
-        const bool odd_buf = out_buffer(d, fused != 0) == 1;
+        const bool odd_buf = out_buffer(d) == 1;
         if (odd_buf) tiles = (uint32_t)(((int64_t)len + kMergeTile - 1) / kMergeTile);
         else if (desc) tiles = (uint32_t)(((int64_t)len / 2 + kMergeTile - 1) / kMergeTile);
         if (tiles) {
@@ -481,16 +477,10 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         }
       } else {
         const int d = ndepth[x];
-        // binary passes: output tiles of kMergeTile; fused passes: chunk-boundary slots
-        const uint32_t tiles = fused ? (uint32_t)(size / kChunkSpan + 2)
-                                     : (uint32_t)((hi - 1) / merge_tile - lo / merge_tile + 1);
+        // output tiles: from lo to the next multiple of merge_tile, then whole tiles
+        const uint32_t tiles = (uint32_t)((hi - 1) / merge_tile - lo / merge_tile + 1);
         if (d >= kMaxLevels) {
           post_status(&hdr->status, nullptr, kDevInternal);
-        } else if (fused && (d & 1)) {
-          // odd depth: merged inside the fused pass of its parent; record where it splits
-          if (par < 0) post_status(&hdr->status, nullptr, kDevInternal);
-          else if (par == nodeR[x]) lsplit[par] = S[x];  // x is the left child of nodeR[x]
-          else rsplit[par] = S[x];
         } else {
           const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
@@ -604,8 +594,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     if (e != cudaSuccess) return e;
     plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                             c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
-                                            c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
-                                            c.lsplit, c.rsplit, c.merge_tile, c.hdr);
+                                            c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.merge_tile,
+                                            c.hdr);
     return cudaGetLastError();
   }
   node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
@@ -626,8 +616,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
-                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.fused ? 1 : 0,
-                                          c.lsplit, c.rsplit, c.merge_tile, c.hdr);
+                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.merge_tile,
+                                          c.hdr);
   return cudaGetLastError();
 }
 

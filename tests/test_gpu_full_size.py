@@ -2,11 +2,11 @@
 (ps_sort_ws with a workspace from PyTorch's allocator).
 
 n = 1e8 single arrays are compared with the CPU oracle element by element (the oracle sorts
-them in seconds).  The 10,000-segment batched input (about 1.26e9 keys) is checked by
-properties that together determine the stable sort uniquely -- every segment is sorted, every
-output element is the input element its payload names, each payload index appears once and
-stays in its segment, and equal keys keep payload order -- plus sampled segments against the
-oracle."""
+them in seconds).  The 10,000-segment batched input (about 1.23e9 keys) is checked on the
+device by properties that together determine the stable sort uniquely -- every segment is
+sorted, every output element is the input element its payload names, each payload index appears
+once and stays in its segment, and equal keys keep payload order -- and then compared with the
+oracle's segmented sort element by element, together with its whole segmented plan."""
 import numpy as np
 import pytest
 import torch
@@ -94,14 +94,22 @@ def test_full_segmented_10k(ps):
     assert bool(((dk[1:] >= dk[:-1]) | ~same).all())
     eq = same & (dk[1:] == dk[:-1])
     assert bool(((idx[1:] > idx[:-1]) | ~eq).all())
-    # sampled segments against the oracle
-    rng = np.random.default_rng(0)
     hk = dk.cpu().numpy()
     hv = dv.cpu().numpy().view(np.uint32)
-    for s in rng.choice(10000, size=40, replace=False):
-        a, b = int(off[s]), int(off[s + 1])
-        ref = oracle.powersort(keys[a:b], vals[a:b])
-        assert np.array_equal(hk[a:b], ref.keys) and np.array_equal(hv[a:b], ref.vals)
+    del dk, dv, orig, pos, seg, idx, same, eq
+    # the whole batch against the oracle: every segment sorted by Alg. 2 on its own, element by
+    # element, and the segmented plan (runs, directions, powers with 0 between segments, leaf
+    # depths, merge cost) from ps_analyze with the same offsets
+    ref = oracle.sort_segmented(keys, vals, off)
+    assert np.array_equal(hk, ref[0]) and np.array_equal(hv, ref[1])
+    del hk, hv
+    an = ps.ps_analyze(_dev(keys), offsets=doff, key_type=0)
+    assert an["runs"] == ref[2].size - 1
+    assert np.array_equal(an["starts"], ref[2])
+    assert np.array_equal(an["desc"], ref[3])
+    assert np.array_equal(an["power"].astype(np.int32), ref[4])
+    assert np.array_equal(an["leaf_depth"].astype(np.int32), ref[5])
+    assert an["cost"] == ref[6]
 
 
 @pytest.mark.parametrize("mean_len", [3000, 100000])

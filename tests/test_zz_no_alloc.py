@@ -1,17 +1,19 @@
 """ps_sort_noalloc: the allocation-free entry point for callers that must not allocate device
 memory while they run (its scratch is one fixed array in the library's device image).
 
-Checked through the C ABI against the regular entry point (ps_sort_ws with a workspace from
-PyTorch's allocator): the results must be identical, bit for bit, on two calls in a row, and a
-size beyond the fixed maximum must be refused without touching the data.  This file is
-collected last on purpose, and it must pass both alone in a fresh process and after the other
-tests."""
+Every result is compared with the CPU oracle's powersort element by element (keys and
+payloads, so the order of equal keys too), and with the regular entry point (ps_sort with a
+workspace from the library's pool) beside it, on two calls in a row.  A warm call must leave the
+device's free memory unchanged, and a size beyond the fixed maximum must be refused without
+touching the data.  This file is collected last on purpose, and it must pass both alone in a
+fresh process and after the other tests."""
 import ctypes
 
 import numpy as np
 import pytest
 import torch
 
+import oracle
 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -48,26 +50,54 @@ def _noalloc_sort(lib, keys: torch.Tensor, vals: torch.Tensor | None, kt: int) -
     return st
 
 
-def test_noalloc_matches_regular_entry_two_calls_in_a_row(lib):
+def _host(t: torch.Tensor, dtype) -> np.ndarray:
+    return t.cpu().numpy().view(dtype)
+
+
+def test_noalloc_matches_oracle_two_calls_in_a_row(lib):
     # call 1: int32 runs with payload; call 2: uint64 keys with dense duplicates at the maximum size
     k1, v1 = workloads.runs_i32(200003, seed=31)
     k2, v2 = workloads.pareto_u64(PS_NOALLOC_MAX_N, seed=32, distinct=1000)
-    inputs = [(torch.from_numpy(k1).cuda(), torch.from_numpy(v1.view(np.int32)).cuda(), 0),
-              (torch.from_numpy(k2.view(np.int64)).cuda(), torch.from_numpy(v2.view(np.int32)).cuda(), 2)]
-    for dk, dv, kt in inputs:
+    inputs = [(k1, v1, "i32", 0, torch.from_numpy(k1).cuda(), torch.from_numpy(v1.view(np.int32)).cuda()),
+              (k2, v2, "u64", 2, torch.from_numpy(k2.view(np.int64)).cuda(),
+               torch.from_numpy(v2.view(np.int32)).cuda())]
+    for hk, hv, name, kt, dk, dv in inputs:
+        ref = oracle.powersort(hk, hv, kt=name)
         want_k, want_v = _reference_sort(dk, dv, kt)
         assert _noalloc_sort(lib, dk, dv, kt) == 0
+        np.testing.assert_array_equal(_host(dk, hk.dtype), ref.keys)
+        np.testing.assert_array_equal(_host(dv, np.uint32), ref.vals)
         assert torch.equal(dk, want_k)
         assert torch.equal(dv, want_v)
 
 
 def test_noalloc_keys_only_and_repeat(lib):
     k, _ = workloads.perm_i32(100000, seed=33)
+    ref = oracle.powersort(k, None, kt="i32")
     for _ in range(2):
         dk = torch.from_numpy(k).cuda()
         want_k, _ = _reference_sort(dk, None, 0)
         assert _noalloc_sort(lib, dk, None, 0) == 0
+        np.testing.assert_array_equal(_host(dk, np.int32), ref.keys)
         assert torch.equal(dk, want_k)
+
+
+def test_noalloc_allocates_nothing(lib):
+    """After a first call of the same key type and payload choice (kernel modules loaded), a call
+    leaves the device's free memory exactly as it was."""
+    k, v = workloads.runs_i32(150001, seed=35)
+    ref = oracle.powersort(k, v, kt="i32")
+    dk = torch.from_numpy(k).cuda()
+    dv = torch.from_numpy(v.view(np.int32)).cuda()
+    warm_k, warm_v = dk.clone(), dv.clone()
+    assert _noalloc_sort(lib, warm_k, warm_v, 0) == 0
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    assert _noalloc_sort(lib, dk, dv, 0) == 0
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
+    np.testing.assert_array_equal(_host(dk, np.int32), ref.keys)
+    np.testing.assert_array_equal(_host(dv, np.uint32), ref.vals)
 
 
 def test_noalloc_refuses_sizes_beyond_its_scratch(lib):
