@@ -13,13 +13,14 @@ events between a barrier + synchronize on both sides, max over ranks.  Also repo
                  per merge output) over its CUDA-event time inside the timed region, against the
                  measured HBM copy bandwidth; plus the whole sort against the merge-cost
                  roofline M x 8 B x 2 / bandwidth (M = exact merge cost of the detected runs).
-  * e2e       -- the same metric through the package's host-array pipeline (HostSortPipeline over
-                 the device-driven C-ABI sort): pinned host input -> device, sort, device ->
-                 pinned host output, every step, four arrays in flight.
+  * e2e       -- the same metric through the C ABI's host-buffer call ps_sort_host_ws: every step
+                 copies one pinned host array in, sorts it and copies it out to pinned host
+                 memory, four streams with one caller-owned device buffer set each (the package's
+                 HostSortPipeline and the serial ps_sort_host are reported beside it).
   * cpu_baseline -- the CPU oracle (single-threaded plain C++ powersort) on one input of the same
                  workload on the host cores.
---impl reference: the oracle as the reference arm, each step a bounded sample (the first
-10^7 keys of the same workload).
+--impl reference: the oracle as the reference arm, each step one full n = 10^8 input of the
+same workload (the headline configuration), single thread.
 Multi-GPU (torchrun): independent replicas, one array per rank, no collective on the data path.
 """
 from __future__ import annotations
@@ -43,7 +44,6 @@ SEED = 42
 WORKLOAD = "plain powersort, n=1e8 int32 keys + uint32 payload, run lengths uniform in [1, 2*sqrt(n)], " \
            "sorted uniform int32 per run, 25% of runs descending"
 FALLBACK_HBM_GBS = 6800.0
-REF_SAMPLE = 10 ** 7
 
 
 def _peaks():
@@ -141,6 +141,25 @@ def _cpu_baseline(keys, vals, sample_desc: str):
             "sample": sample_desc, "seconds": dt, "merge_cost": res.cost, "runs": res.r}
 
 
+def check_sorted_device(out_k, out_v, in_k) -> bool:
+    """The output is the unique stable sort of the input: keys non-decreasing, every output key is
+    the input key its payload (the original index) names, every index appears once, and equal
+    keys keep increasing indices."""
+    import torch
+    n = out_k.numel()
+    idx = out_v.to(torch.int64) & 0xFFFFFFFF
+    if not bool((out_k[1:] >= out_k[:-1]).all()):
+        return False
+    if not torch.equal(in_k[idx], out_k):
+        return False
+    seen = torch.zeros(n, dtype=torch.int32, device=out_k.device)
+    seen.index_add_(0, idx, torch.ones(n, dtype=torch.int32, device=out_k.device))
+    if not bool((seen == 1).all()):
+        return False
+    eq = out_k[1:] == out_k[:-1]
+    return bool(((idx[1:] > idx[:-1]) | ~eq).all())
+
+
 def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tree: int = 0, min_run: int = 1):
     """Sort throughput of one more workload (resident inputs, fresh copy per step); tree 1 uses
     peeksort's merge tree (Alg. 1) instead of powersort's; min_run > 1 extends short runs to that
@@ -192,6 +211,10 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
     k0 = torch.from_numpy(keys).to(dev)
     v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
     doff = torch.from_numpy(off).to(dev)
+    an = ps.ps_analyze(k0, offsets=doff, key_type=ps.PS_KEY_I32)  # merge cost of all segments' trees
+    M = int(an["cost"])
+    peak, peak_kind = _peaks()
+    ideal_ms = M * 8 * 2 / (peak * 1e9) * 1e3
     dk, dv = k0.clone(), v0.clone()
     ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n, True), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -256,6 +279,9 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
             "plain_loop_ms": plain_ms, "plain_gkeys_s": n / (plain_ms / 1e3) / 1e9,
             "speedup": plain_ms / batched_ms, "identical_results": identical,
             "graph_ms": gbest, "graph_gkeys_s": n / (gbest / 1e3) / 1e9, "graph_identical_results": graph_identical,
+            "merge_cost_roofline": {"M": M, "runs": int(an["runs"]), "bytes": M * 16, "ideal_ms": ideal_ms,
+                                    "frac": ideal_ms / batched_ms, "graph_frac": ideal_ms / gbest,
+                                    "peak_gbs": peak, "peak_kind": peak_kind},
             "batched_entry": "ps_sort_segmented_ws (one call)",
             "graph_entry": "ps_sort_async_ws captured once in a CUDA graph, replayed",
             "plain_entry": "ps_sort_ws per array"}
@@ -276,6 +302,12 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
         k, v = workloads.pareto_f32(m, seed=SEED * 7919 + i, alpha=1.5, special_frac=0.01)
         reqs.append((torch.from_numpy(k.view(np.int32)).pin_memory(), torch.from_numpy(v.view(np.int32)).pin_memory()))
     total = sum(k.numel() for k, _ in reqs)
+    # merge cost of every request's own tree (the work the served batches must do)
+    M = 0
+    for k, _ in reqs:
+        M += int(ps.ps_analyze(k.to(dev), key_type=ps.PS_KEY_F32)["cost"])
+    peak, peak_kind = _peaks()
+    ideal_s = M * 8 * 2 / (peak * 1e9)
     outs = [(torch.empty_like(k, pin_memory=True), torch.empty_like(v, pin_memory=True)) for k, v in reqs]
     stream = torch.cuda.current_stream(dev)
 
@@ -300,7 +332,12 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
     warm.close()
     out = {"workload": f"{nreq} float32 requests, sizes floor(2^U(10,24)), ~1% NaN/+-0 (totalOrder), "
                        "Pareto(1.5) runs, uint32 payload, Poisson arrivals", "keys": int(total),
-           "plain_capacity_req_s": capacity, "plain_back_to_back_gkeys_s": total / plain_busy / 1e9, "loads": {}}
+           "plain_capacity_req_s": capacity, "plain_back_to_back_gkeys_s": total / plain_busy / 1e9,
+           "merge_cost_roofline": {"M": M, "bytes": M * 16, "ideal_ms": ideal_s * 1e3, "peak_gbs": peak,
+                                   "peak_kind": peak_kind, "plain_back_to_back_frac": ideal_s / plain_busy,
+                                   "note": "frac = ideal device time of all merges / wall time of the whole "
+                                           "trace; every request also crosses the host link twice"},
+           "loads": {}}
     for load in loads:
         lam = load * capacity
         gaps = rng.exponential(1.0 / lam, size=nreq)
@@ -320,6 +357,7 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
         srv.close()
         sb = latency_stats(handles)
         sb["batches"] = srv.batches
+        sb["merge_cost_roofline_frac"] = ideal_s / sb["wall_s"] if sb.get("wall_s") else None
         sb["server"] = {"slots": len(srv._free), "max_batch_keys": srv.cap, "held_bytes": srv.held_bytes}
         # sequential plain launches on the same arrival trace
         lat = []
@@ -334,7 +372,8 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
         wall = time.perf_counter() - start
         lat = np.array(lat) * 1e3
         sp = {"keys_per_s": total / wall, "p50_ms": float(np.percentile(lat, 50)),
-              "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "wall_s": wall}
+              "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()), "wall_s": wall,
+              "merge_cost_roofline_frac": ideal_s / wall}
         out["loads"][str(load)] = {"arrival_rate_req_s": lam, "batched": sb, "plain": sp}
     return out
 
@@ -347,9 +386,8 @@ def run_reference(args):
     import workloads
     oracle.build()
     workloads.build()
-    n_s = min(REF_SAMPLE, args.n)
-    keys, vals = workloads.runs_i32(n_s, SEED, max_len=int(2 * (args.n ** 0.5)))
-    import numpy as np
+    n_s = args.n
+    keys, vals = _gen(n_s, SEED)
     for _ in range(args.warmup):
         oracle.powersort(keys, vals)
     times = []
@@ -359,12 +397,12 @@ def run_reference(args):
         times.append(time.perf_counter() - t)
     total = sum(times)
     value = n_s * args.steps / total / 1e9
-    sample = f"first {n_s} keys of the n={args.n} workload (same seed and run-length law), per step"
+    sample = f"one full n={n_s} input of the headline workload per step (the GPU arm's seed), oracle powersort (Alg. 2)"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": args.n, "sample_n": n_s,
+            "config": {"workload": WORKLOAD, "n": args.n, "sample_n": n_s, "same_config": n_s == args.n,
                        "parallelism": "replicas (reference runs on rank 0 only)"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -471,9 +509,9 @@ def run_gpu(args):
     clocks = sampler.stop()
     assert ps.ps_stream_status() == 0, "device reported an error"
 
-    # correctness of the timed outputs (cheap device-side checks on the last copy)
+    # correctness of the timed outputs: the last copy is the unique stable sort of the input
     k, v = copies[(args.steps - 1) % ncopies]
-    ok = bool((k[1:] >= k[:-1]).all().item())
+    ok = check_sorted_device(k, v, dk0)
     total_ms = max_over_ranks(total_ms, dist, dev)
     ms_per_step = total_ms / args.steps
     value = replica_throughput(ws, n, args.steps, total_ms)
@@ -525,53 +563,77 @@ def run_gpu(args):
             "sorted_check": ok}
 
     # end to end through the C ABI with host buffers (pinned), every step H2D + sort + D2H:
-    # ps_sort_host_ws on three streams with one device buffer set each, so the copy-in of one
-    # step, the sort of another and the copy-out of a third overlap (the way a caller sorting a
-    # stream of host arrays uses it); the serial single-stream ps_sort_host figure is kept too
+    # ps_sort_host_ws on four streams with one caller-owned device buffer set each, so the
+    # copy-in of one step, the sort of another and the copy-out of a third overlap (the way a
+    # caller sorting a stream of host arrays uses it); HostSortPipeline (the package's wrapper
+    # with copies in submission order) and the serial single-stream ps_sort_host are kept too
     if not args.no_e2e:
         del copies
         torch.cuda.empty_cache()
         copies = None
         hk_in = torch.from_numpy(keys).pin_memory()
         hv_in = torch.from_numpy(vals.view(np.int32)).pin_memory()
-        from paper_1805_04154_gb300.pipeline import HostSortPipeline
         depth = 4
-        pipe = HostSortPipeline(n, torch.int32, True, depth=depth, device=dev)
         outs = [(torch.empty_like(hk_in).pin_memory(), torch.empty_like(hv_in).pin_memory()) for _ in range(depth)]
         e2e_steps = max(4 * depth, min(args.steps, 24))
+        sets = [(torch.empty(n, dtype=torch.int32, device=dev), torch.empty(n, dtype=torch.int32, device=dev),
+                 torch.empty(wsb, dtype=torch.uint8, device=dev), torch.cuda.Stream(dev)) for _ in range(depth)]
 
-        def e2e_step(i):
+        def abi_step(i):
+            q = i % depth
+            kd, vd, wd, st_ = sets[q]
+            ps.ps_sort_host_ws(ps.PS_KEY_I32, hk_in.data_ptr(), hv_in.data_ptr(), outs[q][0].data_ptr(),
+                               outs[q][1].data_ptr(), n, kd, vd, wd, stream=st_)
+
+        def timed_loop(submit, streams, count):
+            """Median of three repetitions (the host link is shared with the machine's other GPUs,
+            so single runs vary); events on the first stream, the others joined to it."""
+            reps_ms = []
+            for _ in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(streams[0])
+                for st_ in streams[1:]:
+                    st_.wait_event(e0)
+                for i in range(count):
+                    submit(i)
+                for st_ in streams[1:]:
+                    ev = torch.cuda.Event()
+                    ev.record(st_)
+                    streams[0].wait_event(ev)
+                e1.record(streams[0])
+                torch.cuda.synchronize(dev)
+                reps_ms.append(max_over_ranks(e0.elapsed_time(e1), dist, dev))
+            return sorted(reps_ms)[1], reps_ms
+
+        for i in range(depth):
+            abi_step(i)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        launches_e2e0 = ps.ps_launch_count()
+        e2e_ms, reps_ms = timed_loop(abi_step, [st_ for (_, _, _, st_) in sets], e2e_steps)
+        e2e_launches = (ps.ps_launch_count() - launches_e2e0) // (3 * e2e_steps)
+        assert ps.ps_stream_status() == 0, "device reported an error"
+        ok_e2e = all(check_sorted_device(o[0].to(dev), o[1].to(dev), dk0) for o in outs)
+        del sets
+        torch.cuda.empty_cache()
+        # the package's HostSortPipeline over the same C-ABI sort
+        from paper_1805_04154_gb300.pipeline import HostSortPipeline
+        pipe = HostSortPipeline(n, torch.int32, True, depth=depth, device=dev)
+
+        def pipe_step(i):
             q = i % depth
             pipe.submit(hk_in, hv_in, outs[q][0], outs[q][1])
 
         for i in range(depth):
-            e2e_step(i)
+            pipe_step(i)
         pipe.synchronize()
         torch.cuda.synchronize(dev)
-        if dist:
-            dist.barrier()
-        streams = [st_ for (_, _, _, st_) in pipe._sets]
-        # three repetitions of the timed loop; the median is reported (the host link is shared
-        # with the machine's other GPUs, so single runs vary)
-        reps_ms = []
-        for _ in range(3):
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(streams[0])
-            for st_ in streams[1:]:
-                st_.wait_event(e0)
-            for i in range(e2e_steps):
-                e2e_step(i)
-            for st_ in streams[1:]:
-                ev = torch.cuda.Event()
-                ev.record(st_)
-                streams[0].wait_event(ev)
-            e1.record(streams[0])
-            torch.cuda.synchronize(dev)
-            pipe.synchronize()
-            reps_ms.append(max_over_ranks(e0.elapsed_time(e1), dist, dev))
-        e2e_ms = sorted(reps_ms)[1]
-        ok_e2e = all(bool(np.all(o[0].numpy()[1:] >= o[0].numpy()[:-1])) for o in outs)
+        pipe_ms, pipe_reps = timed_loop(pipe_step, [st_ for (_, _, _, st_) in pipe._sets], e2e_steps)
+        pipe.synchronize()
+        del pipe
+        torch.cuda.empty_cache()
         # serial: one ps_sort_host call at a time (synchronous, pool workspace)
         hk_out, hv_out = outs[0]
         ps.ps_sort_host_ptr(ps.PS_KEY_I32, hk_in.data_ptr(), hv_in.data_ptr(), hk_out.data_ptr(),
@@ -591,12 +653,17 @@ def run_gpu(args):
                        "h2d_bytes_per_step": n * eb, "d2h_bytes_per_step": n * eb, "steps": e2e_steps,
                        "ms_per_step": e2e_ms / e2e_steps,
                        "repetitions_ms_per_step": [x / e2e_steps for x in reps_ms],
-                       "entry": "HostSortPipeline (pinned host buffers; copy-in, device-driven sort and copy-out "
-                                "of 4 arrays in flight, copies in each direction in submission order)",
+                       "entry": "ps_sort_host_ws (C ABI; pinned host buffers, 4 streams with one caller-owned "
+                                "device buffer set each; copy-in, device-driven sort and copy-out per call)",
+                       "gpu_launches_per_step": int(e2e_launches),
+                       "pipeline": {"entry": "HostSortPipeline (4 arrays in flight, copies in each direction in "
+                                             "submission order)", "ms_per_step": pipe_ms / e2e_steps,
+                                    "value": replica_throughput(ws, n, e2e_steps, pipe_ms),
+                                    "repetitions_ms_per_step": [x / e2e_steps for x in pipe_reps]},
                        "serial": {"entry": "ps_sort_host (one call at a time)", "ms_per_step": serial_ms,
                                   "value": n / (serial_ms / 1000.0) / 1e9},
                        "sorted_check": ok_e2e}
-        del pipe, outs
+        del outs
         torch.cuda.empty_cache()
 
     if rank == 0 and ws == 1 and not args.no_variants:
