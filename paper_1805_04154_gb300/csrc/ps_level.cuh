@@ -26,6 +26,10 @@ namespace ps {
 //  * warps 0-7 (consumers) wait for a full stage, merge its IPT outputs per thread
 //    (co-rank inside shared memory, then a serial stable merge), write them with 128-bit
 //    stores, and release the stage on its "empty" mbarrier.
+// A child that is a large strictly descending run (a leaf of even depth, flagged in the node
+// item's 4th field: bit 0 left child, bit 1 right child) is still in its original order in the
+// source buffer; the pass reads it backwards: its sorted element i is the element at the end of
+// its range minus i, for the co-rank probes, the copied ranges and the consumers' reads.
 // A ring of NS stages: the copies of the next NS-1 tiles overlap the merge of the current one.
 // All waits are bounded; a timeout posts kDevTimeout and the CTA drains its copies and exits.
 // ---------------------------------------------------------------------------------------
@@ -33,7 +37,8 @@ constexpr int kLevelThreads = kMergeThreads + 64;  // 8 consumer warps + issuer 
 constexpr int kQueue = 8;                          // searched tiles the searcher may run ahead
 constexpr int kSearchBatch = 4;                    // tiles searched together (8 lanes each)
 
-// A searched tile: its node (lo, mid, hi, boundary), outputs [g0, g1), left elements [i0, i1).
+// A searched tile: its node (lo, mid, hi, reversed-children flags), outputs [g0, g1), left
+// elements [i0, i1).
 struct QueuedTile {
   int4 nd;
   int32_t g0, g1, i0, i1;
@@ -43,7 +48,22 @@ struct StageDesc {
   int32_t g0, g1, i0, i1;   // outputs [g0, g1); left elements [i0, i1) of the node
   int32_t lo, mid, la, lb;  // node [lo, mid) + [mid, hi)
   int32_t aoff, boff, vaoff, vboff;  // smem element offsets of A[i0], B[j0] (keys / payloads)
-  int32_t pad[4];
+  int32_t rev;              // bit 0: the left child is read backwards, bit 1: the right child
+  int32_t pad[3];
+};
+
+// Position of sorted element i of a node's left / right child: lo + i (mid + i) for a child in
+// order, mid - 1 - i (hi - 1 - i) for a descending run read backwards.  Computed from the node
+// item itself, so the searches keep no extra pointers live.
+__device__ __forceinline__ int32_t left_at(const int4& nd, int32_t i) { return (nd.w & 1) ? nd.y - 1 - i : nd.x + i; }
+__device__ __forceinline__ int32_t right_at(const int4& nd, int32_t j) { return (nd.w & 2) ? nd.z - 1 - j : nd.y + j; }
+
+template <class T>
+struct ChildSeq {  // a child of node nd in the source buffer, indexed in sorted order
+  const T* __restrict__ src;
+  int4 nd;
+  bool right;
+  __device__ __forceinline__ T operator[](int32_t i) const { return src[right ? right_at(nd, i) : left_at(nd, i)]; }
 };
 
 template <class K, bool V, int NS, int IPT>
@@ -67,9 +87,8 @@ struct PassLayout {
 };
 
 // smallest i in [a, b] with i == b or A[i] > B[diag-1-i], by a 32-way warp search in global memory
-template <class K>
-__device__ __forceinline__ int32_t warp_corank(const typename K::T* __restrict__ A, const typename K::T* __restrict__ B,
-                                               int32_t diag, int32_t a, int32_t b) {
+template <class K, class SA, class SB>
+__device__ __forceinline__ int32_t warp_corank(const SA& A, const SB& B, int32_t diag, int32_t a, int32_t b) {
   const int lane = threadIdx.x & 31;
   while (a < b) {
     const int32_t span = b - a;
@@ -117,6 +136,101 @@ __device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
   while (!mbar_try_wait(bar, parity))
     if (++tries > kMbarTries) return false;
   return true;
+}
+
+// Reverse the staged elements [off, off + len) of a tile's keys (and payloads at voff) in place,
+// spread over the kMergeThreads consumers: a child read backwards is staged in memory order,
+// and this puts its sorted elements in order before the merge.
+template <class T, bool V, int KCAP, int VCAP>
+__device__ __forceinline__ void reverse_staged(T* sk, uint32_t* sv, int32_t off, int32_t voff, int32_t len, int tid) {
+  for (int32_t k = tid; k < len / 2; k += kMergeThreads) {
+    const int32_t x = off + k, y = off + len - 1 - k;
+    if (PS_IN_RANGE(x, KCAP) && PS_IN_RANGE(y, KCAP)) {
+      const T t = sk[x];
+      sk[x] = sk[y];
+      sk[y] = t;
+    }
+    if (V) {
+      const int32_t vx = voff + k, vy = voff + len - 1 - k;
+      if (PS_IN_RANGE(vx, VCAP) && PS_IN_RANGE(vy, VCAP)) {
+        const uint32_t u = sv[vx];
+        sv[vx] = sv[vy];
+        sv[vy] = u;
+      }
+    }
+  }
+}
+
+// One consumer thread's share of a staged tile: the co-rank of its first output inside shared
+// memory, a serial stable merge of up to IPT outputs (the heads of both inputs kept in
+// registers: one shared-memory key read per output), and 128-bit stores.
+template <class K, bool V, int IPT, class Lay>
+__device__ __forceinline__ void consume_tile(const StageDesc& d, const uint8_t* stage, typename K::T* __restrict__ dstk,
+                                             uint32_t* __restrict__ dstv, int tid) {
+  typedef typename K::T T;
+  constexpr int KU = Lay::KU;
+  const T* A = (const T*)stage + d.aoff;
+  const T* B = (const T*)stage + d.boff;
+  const uint32_t* sv = (const uint32_t*)(stage + Lay::kKeyBytes);
+  const int32_t len = d.g1 - d.g0, la = d.i1 - d.i0, lb = len - la;
+  const int32_t diag = tid * IPT;
+  if (diag >= len) return;
+  int32_t i = corank_serial<K>(A, B, la, lb, diag);
+  int32_t j = diag - i;
+  const int32_t cnt = min(IPT, len - diag);
+  T key[IPT];
+  uint32_t val[IPT];
+  T a = A[min(i, la - 1 >= 0 ? la - 1 : 0)], b = B[min(j, lb - 1 >= 0 ? lb - 1 : 0)];
+  auto step = [&](int q) {
+    const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
+    key[q] = takeA ? a : b;
+    if (V) {
+      const int32_t vi = takeA ? d.vaoff + i : d.vboff + j;
+      val[q] = PS_IN_RANGE(vi, Lay::VCAP) ? sv[vi] : 0u;
+    }
+    i += takeA ? 1 : 0;
+    j += takeA ? 0 : 1;
+    if (takeA) {
+      if (i < la && PS_IN_RANGE(d.aoff + i, Lay::KCAP)) a = A[i];
+    } else {
+      if (j < lb && PS_IN_RANGE(d.boff + j, Lay::KCAP)) b = B[j];
+    }
+  };
+  if (cnt == IPT) {  // a whole share: no per-output guard
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) step(q);
+  } else {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+      if (q < cnt) step(q);
+  }
+  const int32_t g = d.g0 + diag;
+  if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
+    uint4* o = (uint4*)(dstk + g);
+#pragma unroll
+    for (int q = 0; q < IPT / KU; ++q) {
+      uint4 w;
+      T* wt = (T*)&w;
+#pragma unroll
+      for (int u = 0; u < KU; ++u) wt[u] = key[q * KU + u];
+      o[q] = w;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < IPT; ++q)
+      if (q < cnt) dstk[g + q] = key[q];
+  }
+  if (V) {
+    if (cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
+      uint4* o = (uint4*)(dstv + g);
+#pragma unroll
+      for (int q = 0; q < IPT / 4; ++q) o[q] = make_uint4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < IPT; ++q)
+        if (q < cnt) dstv[g + q] = val[q];
+    }
+  }
 }
 
 // CTAs per SM the register budget is sized for (16 items per thread need more registers).
@@ -173,16 +287,15 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     int32_t slot = 0;
     if (lane == 0) slot = slot_of_tile(tile_off, nitems, t_begin);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    int4 nd = nodes[slot];  // lo, mid, hi, boundary
+    int4 nd = nodes[slot];  // lo, mid, hi, reversed-children flags
     int32_t la = nd.y - nd.x, lb = nd.z - nd.y;
-    const T* A = srck + nd.x;
-    const T* B = srck + nd.y;
     const int32_t k0 = (int32_t)(t_begin - tile_off[slot]);
     int32_t g0 = (k0 == 0) ? nd.x : (nd.x / kTile + k0) * kTile;
     int32_t i0 = 0;
     if (g0 > nd.x) {
       const int32_t diag = g0 - nd.x;
-      i0 = warp_corank<K>(A, B, diag, max(0, diag - lb), min(diag, la));
+      i0 = warp_corank<K>(ChildSeq<T>{srck, nd, false}, ChildSeq<T>{srck, nd, true}, diag, max(0, diag - lb),
+                          min(diag, la));
     }
     // Batches of kSearchBatch tiles: lane group m (8 lanes) finds the end co-rank of the batch's
     // tile m with an 8-way search, all groups at once.  Each window is anchored at the last
@@ -241,14 +354,12 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             sg1 = m_g1[m];
           }
         if (grp < nb) {
-          const T* GA = srck + snd.x;
-          const T* GB = srck + snd.y;
           const int32_t diag = sg1 - snd.x;
           int32_t ga = sa, gb = sb;
           while (ga < gb) {
             const int32_t span = gb - ga;
             const int32_t x = ga + (int32_t)(((int64_t)span * gl) >> 3);
-            const bool gt = !key_le<K>(GA[x], GB[diag - 1 - x]);
+            const bool gt = !key_le<K>(srck[left_at(snd, x)], srck[right_at(snd, diag - 1 - x)]);
             const uint32_t msk = (__ballot_sync(gmask, gt) >> (grp * 8)) & 0xFFu;
             if (msk) {
               const int fl = __ffs(msk) - 1;
@@ -338,8 +449,12 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       const int4 cnd = qt.nd;
       const int32_t cla = cnd.y - cnd.x;
       const int32_t tg0 = qt.g0, tg1 = qt.g1, ti0 = qt.i0, ti1 = qt.i1;
-      const int32_t a0 = cnd.x + ti0, a1 = cnd.x + ti1;
-      const int32_t b0 = cnd.y + (tg0 - cnd.x - ti0), b1 = cnd.y + (tg1 - cnd.x - ti1);
+      const int32_t tj0 = tg0 - cnd.x - ti0, tj1 = tg1 - cnd.x - ti1;  // right-child elements [tj0, tj1)
+      const bool ra = (cnd.w & 1) != 0, rb = (cnd.w & 2) != 0;
+      // memory ranges of the tile's sorted elements (a child read backwards has them mirrored
+      // at the end of its range)
+      const int32_t a0 = ra ? cnd.y - ti1 : cnd.x + ti0, a1 = ra ? cnd.y - ti0 : cnd.x + ti1;
+      const int32_t b0 = rb ? cnd.z - tj1 : cnd.y + tj0, b1 = rb ? cnd.z - tj0 : cnd.y + tj1;
       // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only need
       // natural alignment; a chunk may start up to 15 bytes before a range and end up to 15
       // bytes after it, always inside 16-byte blocks holding range elements)
@@ -361,6 +476,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       d.boff = (ka1 - ka0) + (b0 - kb0);
       d.vaoff = a0 - va0;
       d.vboff = (va1 - va0) + (b0 - vb0);
+      d.rev = cnd.w & 3;  // the consumers reverse these staged ranges before merging
       sdesc[s] = d;
       uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
       T* sk = (T*)stage;
@@ -406,85 +522,16 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       }
       const StageDesc d = sdesc[s];
       const uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
-      const T* A = (const T*)stage + d.aoff;
-      const T* B = (const T*)stage + d.boff;
-      const uint32_t* sv = (const uint32_t*)(stage + Lay::kKeyBytes);
-      const int32_t len = d.g1 - d.g0, la = d.i1 - d.i0, lb = len - la;
-      const int32_t diag = tid * IPT;
-      if (diag < len) {
-        int32_t i = corank_serial<K>(A, B, la, lb, diag);
-        int32_t j = diag - i;
-        const int32_t cnt = min(IPT, len - diag);
-        T key[IPT];
-        uint32_t val[IPT];
-        // heads of both inputs stay in registers: one shared-memory key read per output
-        T a = A[min(i, la - 1 >= 0 ? la - 1 : 0)], b = B[min(j, lb - 1 >= 0 ? lb - 1 : 0)];
-        if (cnt == IPT) {
-#pragma unroll
-          for (int q = 0; q < IPT; ++q) {
-            const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
-            key[q] = takeA ? a : b;
-            if (V) {
-              const int32_t vi = takeA ? d.vaoff + i : d.vboff + j;
-              val[q] = PS_IN_RANGE(vi, Lay::VCAP) ? sv[vi] : 0u;
-            }
-            i += takeA ? 1 : 0;
-            j += takeA ? 0 : 1;
-            if (takeA) {
-              if (i < la && PS_IN_RANGE(d.aoff + i, Lay::KCAP)) a = A[i];
-            } else {
-              if (j < lb && PS_IN_RANGE(d.boff + j, Lay::KCAP)) b = B[j];
-            }
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < IPT; ++q) {
-            if (q < cnt) {
-              const bool takeA = (j >= lb) || (i < la && key_le<K>(a, b));
-              key[q] = takeA ? a : b;
-              if (V) {
-              const int32_t vi = takeA ? d.vaoff + i : d.vboff + j;
-              val[q] = PS_IN_RANGE(vi, Lay::VCAP) ? sv[vi] : 0u;
-            }
-              i += takeA ? 1 : 0;
-              j += takeA ? 0 : 1;
-              if (takeA) {
-                if (i < la && PS_IN_RANGE(d.aoff + i, Lay::KCAP)) a = A[i];
-              } else {
-                if (j < lb && PS_IN_RANGE(d.boff + j, Lay::KCAP)) b = B[j];
-              }
-            }
-          }
-        }
-        const int32_t g = d.g0 + diag;
-        if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
-          uint4* o = (uint4*)(dstk + g);
-#pragma unroll
-          for (int q = 0; q < IPT / KU; ++q) {
-            uint4 w;
-            T* wt = (T*)&w;
-#pragma unroll
-            for (int u = 0; u < KU; ++u) wt[u] = key[q * KU + u];
-            o[q] = w;
-          }
-        } else {
-#pragma unroll
-          for (int q = 0; q < IPT; ++q)
-            if (q < cnt) dstk[g + q] = key[q];
-        }
-        if (V) {
-          if (cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
-            uint4* o = (uint4*)(dstv + g);
-#pragma unroll
-            for (int q = 0; q < IPT / 4; ++q)
-              o[q] = make_uint4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
-          } else {
-#pragma unroll
-            for (int q = 0; q < IPT; ++q)
-              if (q < cnt) dstv[g + q] = val[q];
-          }
-        }
+      if (d.rev) {  // uniform over the consumers: they all work on the same tile
+        uint8_t* wstage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
+        T* sk = (T*)wstage;
+        uint32_t* svw = (uint32_t*)(wstage + Lay::kKeyBytes);
+        const int32_t la = d.i1 - d.i0, lb = (d.g1 - d.g0) - la;
+        if (d.rev & 1) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.aoff, d.vaoff, la, tid);
+        if (d.rev & 2) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.boff, d.vboff, lb, tid);
+        consumer_all(true);  // barrier among the consumers: the staged tile is in sorted order
       }
+      consume_tile<K, V, IPT, Lay>(d, stage, dstk, dstv, tid);
       __syncwarp();
       if ((tid & 31) == 0) mbar_arrive(&empty[s]);
     }

@@ -401,8 +401,9 @@ __global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, cons
 // organised around the element count sub_lim that one CTA can merge in shared memory:
 //  * a node or leaf of size <= sub_lim whose parent is larger (or that is a root) is one
 //    "small task": its whole subtree is merged in shared memory;
-//  * larger leaves that must move (odd depth -> scratch buffer, or descending -> reversed) get
-//    placement tiles;
+//  * larger leaves that must move (odd depth -> scratch buffer; descending and alone in their
+//    segment -> reversed in place) get placement tiles; a larger descending leaf of even depth
+//    >= 2 is read backwards by its parent's merge;
 //  * larger internal nodes are merged by HBM passes, one pass per depth.
 // Buffer parity (out_buffer): a node at depth d writes buffer d mod 2 (0 = the caller's arrays)
 // and reads its children from buffer (d+1) mod 2, so every leaf starts in buffer (depth mod 2).
@@ -446,10 +447,14 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
       } else {
         const bool desc = (run_desc[x] & 1) != 0;
         if (run_desc[x] & 2) post_status(&hdr->status, nullptr, kDevInternal);  // extended runs are short
+        // odd depth: copied to the scratch buffer (reversed on the way if descending); a
+        // descending leaf of even depth >= 2 stays where it is and its parent's level pass reads
+        // it backwards; only a descending leaf that is a whole segment (depth 0, no merge above
+        // it) is reversed in place
         uint32_t tiles = 0;
         const bool odd_buf = out_buffer(d) == 1;
         if (odd_buf) tiles = (uint32_t)(((int64_t)len + kMergeTile - 1) / kMergeTile);
-        else if (desc) tiles = (uint32_t)(((int64_t)len / 2 + kMergeTile - 1) / kMergeTile);
+        else if (desc && d == 0) tiles = (uint32_t)(((int64_t)len / 2 + kMergeTile - 1) / kMergeTile);
         if (tiles) {
           const unsigned long long old = atomicAdd(&hdr->leaf_ctr, (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
@@ -482,10 +487,17 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         if (d >= kMaxLevels) {
           post_status(&hdr->status, nullptr, kDevInternal);
         } else {
+          // children that are large descending leaves of even depth are read backwards by the
+          // level pass (bit 0: left child, bit 1: right child); only nodes of odd depth have them
+          int32_t rev = 0;
+          if (d & 1) {
+            if (nodeL[x] == x - 1 && (run_desc[x - 1] & 1) && S[x] - S[x - 1] > sub_lim) rev |= 1;
+            if (nodeR[x] == x + 1 && (run_desc[x] & 1) && S[x + 1] - S[x] > sub_lim) rev |= 2;
+          }
           const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
           if (slot < (uint32_t)level_cap) {
-            level_items[(size_t)d * level_cap + slot] = make_int4(lo, S[x], hi, x);
+            level_items[(size_t)d * level_cap + slot] = make_int4(lo, S[x], hi, rev);
             level_tile_off[(size_t)d * level_cap + slot] = (uint32_t)(old & 0xffffffffu);
             atomicAdd(&hdr->level_elems[d], (unsigned long long)size);
           } else {
