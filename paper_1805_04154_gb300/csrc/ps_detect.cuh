@@ -81,6 +81,16 @@ __device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t co
   return lo;
 }
 
+// Key u of a 16-byte chunk (four 4-byte keys or two 8-byte keys, little-endian).
+template <class T>
+__device__ __forceinline__ T chunk_key(const uint4& w, int u) {
+  if constexpr (sizeof(T) == 4) {
+    return (T)(u == 0 ? w.x : u == 1 ? w.y : u == 2 ? w.z : w.w);
+  } else {
+    return u == 0 ? (T)(((uint64_t)w.y << 32) | w.x) : (T)(((uint64_t)w.w << 32) | w.z);
+  }
+}
+
 // The thread's view of its kDetectItems = 32 consecutive positions p0 .. p0+31:
 //   L  bit q (q = 0..32): key[p0+q-1] <= key[p0+q]  (the pair into position p0+q)
 //   F  bit q (q = 0..32): position p0+q is forced to START (position 0 or a segment start)
@@ -144,17 +154,23 @@ struct ThreadRuns {
       }
     }
   }
-  // The same view for 4-byte keys, the warp's 32 x 32 keys staged through shared memory: each
-  // lane issues eight 16-byte cp.async copies at lane-consecutive addresses (coalesced, no
-  // registers held while they are in flight), then reads its own 32 keys back.  Chunk c of lane
-  // l's 128-byte row is stored at index c ^ (l & 7) of the row, so the copies of a quarter warp
-  // (one row) and the row reads of a quarter warp (eight rows, one chunk index each) both cover
-  // eight distinct 16-byte bank groups.  The pairs into the lane's first position and out of its
-  // last one use the neighbouring lanes' keys.  A warp whose keys (with the look-ahead) are not
-  // wholly inside the array, or whose keys are not 16-byte aligned, takes load().
+  // The same view with the warp's 32 x 32 keys staged through shared memory.  A lane's 32 keys
+  // form a row of 16-byte chunks (8 for 4-byte keys, 16 for 8-byte keys), staged eight chunks
+  // per lane at a time (4 KB per warp; 8-byte keys take two such halves): each lane issues
+  // eight 16-byte cp.async copies at lane-consecutive addresses (eight lanes cover 128
+  // contiguous bytes of one row, so every copy instruction reads whole 128-byte segments and no
+  // registers are held while the copies are in flight), then reads its own eight chunks back.
+  // Chunk c of lane l's staged row is stored at index c ^ (l & 7), so the copies of a quarter
+  // warp (one row) and the row reads of a quarter warp (eight rows, one chunk index each) both
+  // cover eight distinct 16-byte bank groups.  The pairs into the lane's first position and out
+  // of its last one use the neighbouring lanes' keys.  A warp whose keys (with the look-ahead)
+  // are not wholly inside the array, or whose keys are not 16-byte aligned, takes load().
   __device__ __forceinline__ void load_staged(const T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
                                               int32_t count, int32_t tile, int tid, uint4* __restrict__ stage) {
-    static_assert(sizeof(T) == 4 && kDetectItems == 32, "a lane row is 8 chunks of 4 keys");
+    static_assert(kDetectItems == 32, "a lane row is 32 keys");
+    constexpr int kPerChunk = 16 / (int)sizeof(T);         // keys per 16-byte chunk
+    constexpr int kRowChunks = kDetectItems / kPerChunk;   // chunks per lane row: 8 or 16
+    constexpr int kHalves = kRowChunks / 8;                // staged eight chunks per lane at a time
     constexpr int kWarpKeys = 32 * kDetectItems;
     const int lane = tid & 31;
     const int32_t wp0 = tile * kDetectTile + (tid - lane) * kDetectItems;
@@ -163,15 +179,6 @@ struct ThreadRuns {
       return;
     }
     const uint4* __restrict__ src = reinterpret_cast<const uint4*>(keys + wp0);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int g = j * 32 + lane, row = g >> 3, c = g & 7;  // chunk g of the warp's 256
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(stage + row * 8 + (c ^ (row & 7)))),
-                   "l"(src + g)
-                   : "memory");
-    }
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
     p0 = wp0 + lane * kDetectItems;
     nvalid = kDetectItems;
     valid = (1ull << kDetectItems) - 1ull;
@@ -179,14 +186,28 @@ struct ThreadRuns {
     F = 0;
     T first = 0, last = 0;
 #pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const uint4 w = stage[lane * 8 + (v ^ (lane & 7))];
-      const T wt[4] = {w.x, w.y, w.z, w.w};
+    for (int h = 0; h < kHalves; ++h) {
+      if (h > 0) __syncwarp();  // every lane has read the previous half
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (v == 0 && u == 0) first = wt[0];
-        else L |= (uint64_t)(K::ord(last) <= K::ord(wt[u])) << (v * 4 + u);
-        last = wt[u];
+      for (int j = 0; j < 8; ++j) {
+        const int g = j * 32 + lane, row = g >> 3, c = g & 7;  // staged chunk g of the warp's 256
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(stage + row * 8 + (c ^ (row & 7)))),
+                     "l"(src + row * kRowChunks + h * 8 + c)
+                     : "memory");
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncwarp();
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const uint4 w = stage[lane * 8 + (v ^ (lane & 7))];
+#pragma unroll
+        for (int u = 0; u < kPerChunk; ++u) {
+          const T x = chunk_key<T>(w, u);
+          const int q = (h * 8 + v) * kPerChunk + u;
+          if (q == 0) first = x;
+          else L |= (uint64_t)(K::ord(last) <= K::ord(x)) << q;
+          last = x;
+        }
       }
     }
     T before = __shfl_up_sync(0xffffffffu, last, 1);
@@ -262,12 +283,10 @@ detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const in
                      int32_t count, uint64_t* __restrict__ tile_agg, uint64_t* __restrict__ thr_L,
                      uint64_t* __restrict__ thr_F, uint32_t* __restrict__ thr_fn) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
-  constexpr bool kStaged = sizeof(typename K::T) == 4;
-  __shared__ uint4 stage[kStaged ? kDetectThreads / 32 * 256 : 1];  // 4 KB of keys per warp
+  __shared__ uint4 stage[kDetectThreads / 32 * 256];  // 4 KB of staged keys per warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ThreadRuns<K> tr;
-  if constexpr (kStaged) tr.load_staged(keys, n, offsets, count, blockIdx.x, tid, stage + warp * 256);
-  else tr.load(keys, n, offsets, count, blockIdx.x, tid);
+  tr.load_staged(keys, n, offsets, count, blockIdx.x, tid, stage + warp * 256);
   Fn incl = tr.aggregate();
   // the emit pass replays the runs from these instead of reading the keys again
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
