@@ -24,7 +24,10 @@
  *     are stream-ordered: they return once all work is enqueued; argument errors are returned
  *     synchronously.  Each sort synchronizes the stream once, after planning, to size its
  *     launches.  Errors posted later by the device are reported by ps_stream_status.
- *   - Limits: one call sorts fewer than 2^31 elements in total (PS_ERR_UNSUPPORTED otherwise).
+ *   - Limits: one call sorts fewer than 2^32 elements in total, in fewer than 2^31 - 1 runs (only
+ *     segments of one element can come close); PS_ERR_UNSUPPORTED otherwise.  Node powers are then
+ *     at most 32 and every element position fits 64 bits (Appendix B's node-power note: the
+ *     31-bit form of the Java listing is only exact for int-sized arrays).
  *   - Thread safety: calls on different streams may run concurrently; a workspace must not be
  *     shared by calls in flight at the same time.
  */
@@ -41,7 +44,7 @@ extern "C" {
 typedef enum ps_status {
   PS_OK = 0,
   PS_ERR_INVALID_ARG = 1,    /* bad pointer, size, key type, alignment or segment offsets */
-  PS_ERR_UNSUPPORTED = 2,    /* n >= 2^31 */
+  PS_ERR_UNSUPPORTED = 2,    /* n >= 2^32, or 2^31 - 1 runs or more */
   PS_ERR_OUT_OF_MEMORY = 3,  /* workspace allocation failed or workspace too small */
   PS_ERR_CUDA = 4,           /* a CUDA runtime call failed */
   PS_ERR_TIMEOUT = 5,        /* a bounded device wait gave up (results are not valid) */
@@ -75,8 +78,8 @@ size_t ps_workspace_size(int key_type, int has_vals, int64_t n, int segmented);
  * uint32 payload, or NULL), powersort merge order (Alg. 2).  workspace: device memory of at least
  * ps_workspace_size(key_type, vals != NULL, n, 0) bytes, 256-byte aligned, caller-owned.
  * n = 0 or 1 is a no-op.  Errors: PS_ERR_INVALID_ARG (null or misaligned pointers, n < 0, unknown
- * key type), PS_ERR_OUT_OF_MEMORY (workspace too small), PS_ERR_UNSUPPORTED (n >= 2^31),
- * PS_ERR_CUDA, PS_ERR_TIMEOUT. */
+ * key type), PS_ERR_OUT_OF_MEMORY (workspace too small), PS_ERR_UNSUPPORTED (n >= 2^32, or too
+ * many runs), PS_ERR_CUDA, PS_ERR_TIMEOUT. */
 ps_status ps_sort_ws(int key_type, void* keys, uint32_t* vals, int64_t n, void* workspace,
                      size_t workspace_bytes, void* stream);
 
@@ -115,7 +118,7 @@ ps_status ps_merge_cost(const int64_t* run_lengths, int64_t r, uint64_t* out_cos
  * keys: device array (not modified); d_offsets/count as for ps_sort_segmented_ws, or NULL / 1
  * for one array; workspace as for ps_sort_ws (segmented = d_offsets != NULL).  Host outputs,
  * each optional (NULL to skip), capacity n + 1 entries; r = *out_runs:
- *   starts[r+1]     run starts (starts[r] = n)
+ *   starts[r+1]     run starts (int64; starts[r] = n)
  *   desc[r]         1 if the run was strictly descending
  *   power[r+1]      node power of boundary j between runs j-1 and j (0 at j = 0, j = r and at
  *                   segment boundaries)
@@ -126,7 +129,7 @@ ps_status ps_merge_cost(const int64_t* run_lengths, int64_t r, uint64_t* out_cos
  * *out_cost receives M.  Synchronizes the stream. */
 ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d_offsets,
                      int64_t count, void* workspace, size_t workspace_bytes, int64_t* out_runs,
-                     uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power,
+                     uint64_t* out_cost, int64_t* starts, uint8_t* desc, uint8_t* power,
                      uint8_t* leaf_depth, int32_t* node_left, int32_t* node_right,
                      uint8_t* node_depth, void* stream);
 
@@ -156,6 +159,18 @@ ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, c
  * library's status word and returns.  ps_stream_status(stream) then reports PS_ERR_TIMEOUT (and
  * clears it), and the device stays usable. */
 ps_status ps_selftest_wait_timeout(uint32_t polls, void* stream);
+
+/* Failure-path self-test through the production merge kernel (no fault, trap or hang): sorts
+ * keys[0..n) (and vals) as ps_sort_ws does, except that every wait of the level passes polls at
+ * most `polls` times and, in the deepest level pass, CTA 0 never issues the copies of its first
+ * tile, so the consumers' wait on that stage runs out: they post the timeout bit, the CTA's other
+ * waits give up within `polls` polls each, no copy is left in flight, and the kernel returns.
+ * ps_stream_status(stream) then reports PS_ERR_TIMEOUT; the array's contents are unspecified
+ * afterwards and the device stays usable.  workspace as for ps_sort_ws.  PS_ERR_UNSUPPORTED if the
+ * array has no merge large enough for a level pass; PS_ERR_INVALID_ARG for polls = 0; other
+ * errors as for ps_sort_ws. */
+ps_status ps_selftest_level_pass_timeout(int key_type, void* keys, uint32_t* vals, int64_t n, uint32_t polls,
+                                         void* workspace, size_t workspace_bytes, void* stream);
 
 /* Level-pass configuration and its autotuner.  A level pass splits its merges into tiles of
  * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
@@ -203,7 +218,7 @@ ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, 
  * parent the larger of its range ends), as node powers do for Alg. 2. */
 ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
                           int tree, void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
-                          int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                          int64_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
                           int32_t* node_right, uint8_t* node_depth, void* stream);
 
 /* Minimal run length (Sec. 5.1: the tuned implementations extend every run shorter than
@@ -223,7 +238,7 @@ ps_status ps_sort_minrun_ws(int key_type, void* keys, uint32_t* vals, int64_t n,
                             int64_t count, int min_run, void* workspace, size_t workspace_bytes, void* stream);
 ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
                             int min_run, void* workspace, size_t workspace_bytes, int64_t* out_runs,
-                            uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
+                            uint64_t* out_cost, int64_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
                             int32_t* node_left, int32_t* node_right, uint8_t* node_depth, void* stream);
 
 /* Bounds-checked builds.  A library compiled with -DPS_DEBUG (libpowersort_debug.so) compares

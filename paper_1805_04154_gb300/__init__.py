@@ -94,6 +94,7 @@ def load():
                 "ps_tune_set": ([i32, i32, i32, i32], i32),
                 "ps_tune_get": ([i32, i32, vp, vp], i32),
                 "ps_selftest_wait_timeout": ([ctypes.c_uint32, vp], i32),
+                "ps_selftest_level_pass_timeout": ([i32, vp, vp, i64, ctypes.c_uint32, vp, sz, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
                 "ps_analyze_tree": ([i32, vp, i64, vp, i64, i32, vp, sz, vp, vp, vp, vp, vp, vp, vp, vp, vp,
                                      vp], i32),
@@ -325,7 +326,7 @@ def ps_analyze(keys: torch.Tensor, offsets: torch.Tensor | None = None, key_type
     count = _segments(offsets, keys)
     ws = _workspace(ps_workspace_size(kt, False, n, seg, tree), keys.device)
     cap = n + 2
-    out = {"starts": np.empty(cap, np.int32), "desc": np.empty(cap, np.uint8), "power": np.empty(cap, np.uint8),
+    out = {"starts": np.empty(cap, np.int64), "desc": np.empty(cap, np.uint8), "power": np.empty(cap, np.uint8),
            "leaf_depth": np.empty(cap, np.uint8), "node_left": np.empty(cap, np.int32),
            "node_right": np.empty(cap, np.int32), "node_depth": np.empty(cap, np.uint8)}
     runs = ctypes.c_int64(0)
@@ -486,6 +487,18 @@ def ps_tune_get(key_type: int, has_vals: bool) -> tuple[int, int]:
     a, b = ctypes.c_int(0), ctypes.c_int(0)
     _check(load().ps_tune_get(key_type, 1 if has_vals else 0, ctypes.byref(a), ctypes.byref(b)), "ps_tune_get")
     return a.value, b.value
+
+
+def ps_selftest_level_pass_timeout(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
+                                   polls: int = 1 << 12, key_type: int | None = None, stream=None) -> None:
+    """Queue the level-pass timeout self-test on ``keys`` (see include/powersort.h); then
+    ps_stream_status() reports PS_ERR_TIMEOUT and the contents of ``keys`` are unspecified."""
+    kt = _key_type(keys, key_type)
+    _check_vals(vals, keys)
+    _check(load().ps_selftest_level_pass_timeout(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
+                                                 int(polls), _dev_ptr(workspace, "workspace"),
+                                                 _ws_bytes(workspace, keys), _stream_ptr(stream, keys.device)),
+           "ps_selftest_level_pass_timeout")
 
 
 def ps_selftest_wait_timeout(polls: int = 1 << 14, stream=None) -> None:

@@ -44,13 +44,17 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
     return p;
   };
   const size_t kb = (size_t)key_bytes(kt);
-  const size_t N = (size_t)n + 2;
+  // Run-indexed arrays hold N entries: runs 0..r-1 and the boundaries 0..r.  A greedy run is at
+  // least two elements long unless it starts at the last position of its array or segment, so
+  // one array has r <= n/2 + 1 runs; segments of one element each can make r = n.
+  const size_t N = segmented ? (size_t)n + 2 : (size_t)n / 2 + 3;
+  c.run_cap = (int64_t)N;
   c.k[1] = take((((size_t)n * kb + 15) & ~(size_t)15) + 16);
   c.v[1] = vals ? (uint32_t*)take((((size_t)n * 4 + 15) & ~(size_t)15) + 16) : nullptr;
-  c.S = (int32_t*)take(N * 4);
+  c.S = (pos_t*)take(N * 4);
   c.run_desc = (uint8_t*)take(N);
   c.run_seg = segmented ? (int32_t*)take(N * 4) : nullptr;
-  c.P = (uint8_t*)take(N);
+  c.P = (uint8_t*)take(N + 8);  // the tree passes read whole aligned words up to byte r + 3
   c.nodeL = (int32_t*)take(N * 4);
   c.nodeR = (int32_t*)take(N * 4);
   c.ndepth = (uint8_t*)take(N);
@@ -87,7 +91,7 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.leaf_items = (int32_t*)take(cap * 4);
   c.leaf_tile_off = (uint32_t*)take(cap * 4);
   c.level_cap = (int32_t)cap;
-  c.level_items = (int4*)take((size_t)kMaxLevels * cap * sizeof(int4));
+  c.level_items = (NodeItem*)take((size_t)kMaxLevels * cap * sizeof(NodeItem));
   c.level_tile_off = (uint32_t*)take((size_t)kMaxLevels * cap * 4);
   c.hdr = (PlanHeader*)take(sizeof(PlanHeader));
   c.d_entropy = (double*)take(sizeof(double));
@@ -206,7 +210,7 @@ struct StageTimer {
 struct AnalyzeOut {
   int64_t* runs;
   uint64_t* cost;
-  int32_t* starts;
+  int64_t* starts;
   uint8_t* desc;
   uint8_t* power;
   uint8_t* leaf_depth;
@@ -239,6 +243,9 @@ int default_variant() {
 
 std::atomic<int> g_tune[4][2];  // 0 = default
 thread_local int t_variant_override = 0;  // set by the autotuner around its trial sorts
+// Failure self-test (ps_selftest_level_pass_timeout): the poll bound of the level passes and
+// whether the deepest one withholds a stage; set only around that entry point's sort.
+thread_local uint32_t t_selftest_polls = 0;
 
 void apply_pass_config(Ctx& c, int kt, bool vals) {
   int v = t_variant_override;
@@ -264,7 +271,7 @@ ps_status cuda_status(cudaError_t e) {
 ps_status check_args(int kt, const void* keys, const uint32_t* vals, int64_t n) {
   if (!launch_for(kt)) return PS_ERR_INVALID_ARG;
   if (n < 0) return PS_ERR_INVALID_ARG;
-  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n >= kMaxElems) return PS_ERR_UNSUPPORTED;
   if (n > 0 && (!keys || ((uintptr_t)keys % (uintptr_t)key_bytes(kt)) != 0)) return PS_ERR_INVALID_ARG;
   if (vals && ((uintptr_t)vals & 3u) != 0) return PS_ERR_INVALID_ARG;
   return PS_OK;
@@ -301,12 +308,12 @@ ps_status read_plan_header(const Ctx& c, int dev, PlanHeader& h) {
 }
 
 // The counts the merge launches are sized with must fit the plan's arrays: subtree tasks
-// (<= n + 2 slots), large leaves (<= level_cap items, <= n tiles) and, per depth, level-pass
+// (<= run_cap slots), large leaves (<= level_cap items, <= n tiles) and, per depth, level-pass
 // items (<= level_cap) and tiles (a node of size s spans at most s / tile + 2 tiles).  A plan
 // that breaks one of them is reported instead of launched.
 bool plan_counts_ok(const Ctx& c, const PlanHeader& h, int64_t n) {
-  if (h.runs < 1 || h.runs > n) return false;
-  if ((uint64_t)h.n_small > (uint64_t)n + 2) return false;
+  if (h.runs < 1 || h.runs > n || (int64_t)h.runs + 1 > c.run_cap) return false;
+  if ((uint64_t)h.n_small > (uint64_t)c.run_cap) return false;
   if ((h.leaf_ctr >> 32) > (uint64_t)c.level_cap || (h.leaf_ctr & 0xffffffffull) > (uint64_t)n) return false;
   for (int d = 0; d < kMaxLevels; ++d) {
     const uint64_t items = h.level_ctr[d] >> 32, tiles = h.level_ctr[d] & 0xffffffffull;
@@ -348,7 +355,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   c.kt = kt;
   c.key_bytes = key_bytes(kt);
   c.has_vals = vals != nullptr;
-  c.n = (int32_t)n;
+  c.n = n;
   c.offsets = segmented ? d_offsets : nullptr;
   c.count = segmented ? (int32_t)count : 1;
   c.k[0] = keys;
@@ -383,6 +390,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   if (h.status & kDevBadOffsets) return PS_ERR_INVALID_ARG;
   if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
+  if (h.status & kDevTooManyRuns) return PS_ERR_UNSUPPORTED;
   const int32_t r = h.runs;
   if (!plan_counts_ok(c, h, n)) return PS_ERR_INTERNAL;
 
@@ -390,7 +398,9 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     if (an->runs) *an->runs = r;
     if (an->cost) *an->cost = h.cost;
     const size_t R1 = (size_t)r + 1;
-    if (an->starts) PS_TRY(cudaMemcpyAsync(an->starts, c.S, R1 * 4, cudaMemcpyDeviceToHost, s));
+    // run starts are 32-bit on the device (n < 2^32): copied into the upper half of the caller's
+    // int64 array, then widened in place from the front
+    if (an->starts) PS_TRY(cudaMemcpyAsync((uint32_t*)an->starts + R1, c.S, R1 * 4, cudaMemcpyDeviceToHost, s));
     if (an->desc) PS_TRY(cudaMemcpyAsync(an->desc, c.run_desc, (size_t)r, cudaMemcpyDeviceToHost, s));
     if (an->power) PS_TRY(cudaMemcpyAsync(an->power, c.P, R1, cudaMemcpyDeviceToHost, s));
     if (an->leaf_depth) PS_TRY(cudaMemcpyAsync(an->leaf_depth, c.ldepth, (size_t)r, cudaMemcpyDeviceToHost, s));
@@ -400,6 +410,10 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     double ent = 0.0;
     if (an->stats) PS_TRY(cudaMemcpyAsync(&ent, c.d_entropy, sizeof(double), cudaMemcpyDeviceToHost, s));
     PS_TRY(cudaStreamSynchronize(s));
+    if (an->starts) {
+      const uint32_t* narrow = (const uint32_t*)an->starts + R1;
+      for (size_t i = 0; i < R1; ++i) an->starts[i] = (int64_t)narrow[i];
+    }
     if (an->stats) {
       ps_stats* o = an->stats;
       o->n = n;
@@ -427,6 +441,12 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
     StageTimer t(3, s);
     PS_TRY(kl->place(c, (uint32_t)(h.leaf_ctr >> 32), leaf_tiles));
     t.done(2 * h.place_elems * eb, 1);
+  }
+  if (t_selftest_polls) {
+    c.poll_limit = t_selftest_polls;
+    for (int d = kMaxLevels - 1; d >= 0 && c.withhold_depth < 0; --d)
+      if (h.level_ctr[d] & 0xffffffffull) c.withhold_depth = d;
+    if (c.withhold_depth < 0) return PS_ERR_UNSUPPORTED;  // no large merge to withhold a stage of
   }
   for (int d = kMaxLevels - 1; d >= 0; --d) {
     const uint32_t items = (uint32_t)(h.level_ctr[d] >> 32), tiles = (uint32_t)(h.level_ctr[d] & 0xffffffffull);
@@ -459,7 +479,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   c.kt = kt;
   c.key_bytes = key_bytes(kt);
   c.has_vals = vals != nullptr;
-  c.n = (int32_t)n;
+  c.n = n;
   c.offsets = segmented ? d_offsets : nullptr;
   c.count = segmented ? (int32_t)count : 1;
   c.k[0] = keys;
@@ -634,7 +654,7 @@ ps_status ps_merge_cost(const int64_t* run_lengths, int64_t r, uint64_t* out_cos
 
 ps_status ps_analyze(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
                      void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
-                     int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                     int64_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
                      int32_t* node_right, uint8_t* node_depth, void* stream) {
   AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
   const bool seg = d_offsets != nullptr;
@@ -650,6 +670,16 @@ ps_status ps_selftest_wait_timeout(uint32_t polls, void* stream) {
   PS_TRY(launch_wait_timeout_probe(polls, w, (cudaStream_t)stream));
   g_launches += 1;
   return PS_OK;
+}
+
+ps_status ps_selftest_level_pass_timeout(int key_type, void* keys, uint32_t* vals, int64_t n, uint32_t polls,
+                                         void* workspace, size_t workspace_bytes, void* stream) {
+  if (polls == 0) return PS_ERR_INVALID_ARG;
+  t_selftest_polls = polls;
+  const ps_status st = run(key_type, keys, vals, n, nullptr, 1, false, workspace, workspace_bytes,
+                           (cudaStream_t)stream, nullptr);
+  t_selftest_polls = 0;
+  return st;
 }
 
 ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages) {
@@ -766,7 +796,7 @@ ps_status ps_sort_tree_ws(int key_type, void* keys, uint32_t* vals, int64_t n, c
 
 ps_status ps_analyze_tree(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
                           int tree, void* workspace, size_t workspace_bytes, int64_t* out_runs, uint64_t* out_cost,
-                          int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
+                          int64_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth, int32_t* node_left,
                           int32_t* node_right, uint8_t* node_depth, void* stream) {
   AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
   const bool seg = d_offsets != nullptr;
@@ -783,7 +813,7 @@ ps_status ps_sort_minrun_ws(int key_type, void* keys, uint32_t* vals, int64_t n,
 
 ps_status ps_analyze_minrun(int key_type, const void* keys, int64_t n, const int64_t* d_offsets, int64_t count,
                             int min_run, void* workspace, size_t workspace_bytes, int64_t* out_runs,
-                            uint64_t* out_cost, int32_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
+                            uint64_t* out_cost, int64_t* starts, uint8_t* desc, uint8_t* power, uint8_t* leaf_depth,
                             int32_t* node_left, int32_t* node_right, uint8_t* node_depth, void* stream) {
   AnalyzeOut an{out_runs, out_cost, starts, desc, power, leaf_depth, node_left, node_right, node_depth, nullptr};
   const bool seg = d_offsets != nullptr;
@@ -824,6 +854,8 @@ ps_status ps_stream_status(void* stream) {
     if (cudaMemset(w, 0, 4) != cudaSuccess) return PS_ERR_CUDA;
     if (v & kDevBadOffsets) return PS_ERR_INVALID_ARG;
     if (v & kDevTimeout) return PS_ERR_TIMEOUT;
+    if (v & kDevInternal) return PS_ERR_INTERNAL;
+    if (v & kDevTooManyRuns) return PS_ERR_UNSUPPORTED;
     return PS_ERR_INTERNAL;
   }
   return PS_OK;
@@ -833,7 +865,7 @@ ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* val
                           uint32_t* vals_out, int64_t n, void* dev_keys, uint32_t* dev_vals, void* workspace,
                           size_t workspace_bytes, void* stream) {
   if (!launch_for(key_type) || n < 0) return PS_ERR_INVALID_ARG;
-  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n >= kMaxElems) return PS_ERR_UNSUPPORTED;
   if (n > 0 && (!keys_in || !keys_out || !dev_keys)) return PS_ERR_INVALID_ARG;
   if ((vals_in == nullptr) != (vals_out == nullptr) || (vals_in != nullptr) != (dev_vals != nullptr))
     return PS_ERR_INVALID_ARG;
@@ -855,7 +887,7 @@ ps_status ps_sort_host_ws(int key_type, const void* keys_in, const uint32_t* val
 ps_status ps_sort_host(int key_type, const void* keys_in, const uint32_t* vals_in, void* keys_out,
                        uint32_t* vals_out, int64_t n, void* stream) {
   if (!launch_for(key_type) || n < 0) return PS_ERR_INVALID_ARG;
-  if (n >= ((int64_t)1 << 31)) return PS_ERR_UNSUPPORTED;
+  if (n >= kMaxElems) return PS_ERR_UNSUPPORTED;
   if (n > 0 && (!keys_in || !keys_out)) return PS_ERR_INVALID_ARG;
   if ((vals_in == nullptr) != (vals_out == nullptr)) return PS_ERR_INVALID_ARG;
   const size_t kb = (size_t)key_bytes(key_type);
@@ -943,7 +975,7 @@ const char* ps_status_string(ps_status status) {
   switch (status) {
     case PS_OK: return "ok";
     case PS_ERR_INVALID_ARG: return "invalid argument";
-    case PS_ERR_UNSUPPORTED: return "unsupported size (n >= 2^31)";
+    case PS_ERR_UNSUPPORTED: return "unsupported size (n >= 2^32, or 2^31 - 1 runs or more)";
     case PS_ERR_OUT_OF_MEMORY: return "out of device memory / workspace too small";
     case PS_ERR_CUDA: return "CUDA runtime error";
     case PS_ERR_TIMEOUT: return "a bounded device wait timed out";
@@ -1011,7 +1043,7 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   c.kt = kt;
   c.key_bytes = key_bytes(kt);
   c.has_vals = vals != nullptr;
-  c.n = (int32_t)n;
+  c.n = n;
   c.offsets = nullptr;
   c.count = 1;
   c.k[0] = keys;
@@ -1030,6 +1062,7 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   PS_TRY(cudaStreamSynchronize(s));
   if (h.status & kDevTimeout) return PS_ERR_TIMEOUT;
   if (h.status & kDevInternal) return PS_ERR_INTERNAL;
+  if (h.status & kDevTooManyRuns) return PS_ERR_UNSUPPORTED;
   // the same bounds on the plan's counts as every other entry point: a plan that broke them
   // would make the launches below write past their regions of the shared scratch array
   if (!plan_counts_ok(c, h, n)) return PS_ERR_INTERNAL;

@@ -9,10 +9,16 @@
 namespace ps {
 
 // ---------------------------------------------------------------------------------------
-// Sizes.  Positions are int32: one call sorts fewer than 2^31 elements in total, which also
-// keeps every node power below 32 (Definition "Node Power": P <= floor(lg n) + 1).
+// Sizes.  One call sorts fewer than 2^32 elements in total, so every element position fits an
+// unsigned 32-bit integer (pos_t: run starts, node ranges, tile bounds, co-ranks); addresses and
+// the few sums that can pass 2^32 are formed in 64 bits.  Run and boundary indices are int32 (a
+// call has fewer than 2^31 runs); offsets inside a tile or a shared-memory task are int32.  Node
+// powers are at most floor(lg n) + 1 <= 32 (Definition "Node Power"), so node depths are < 32.
 // ---------------------------------------------------------------------------------------
-constexpr int kMaxLevels = 32;  // powers and depths are < 32
+typedef uint32_t pos_t;
+constexpr int64_t kMaxElems = (int64_t)1 << 32;      // n < kMaxElems
+constexpr int32_t kMaxRuns = 0x7ffffffe;            // r <= kMaxRuns (boundary indices 0..r fit int32)
+constexpr int kMaxLevels = 32;  // node depths are < 32
 
 // Stage 1 (run detection): one CTA scans a tile of kDetectTile positions.
 constexpr int kDetectThreads = 256;
@@ -93,6 +99,7 @@ enum DevStatus : uint32_t {
   kDevTimeout = 1u << 0,      // a bounded wait gave up
   kDevBadOffsets = 1u << 1,   // segment offsets not non-decreasing / out of range
   kDevInternal = 1u << 2,     // an internal consistency check failed
+  kDevTooManyRuns = 1u << 3,  // more runs than boundary indices can hold (segments of 1 element)
 };
 
 // What the device tells the host after planning (one D2H copy per sort).
@@ -156,6 +163,13 @@ __device__ __forceinline__ void post_status(uint32_t* hdr_status, uint32_t* lib_
   if (hdr_status) atomicOr(hdr_status, bits);
   if (lib_status) atomicOr(lib_status, bits);
 }
+
+// A merge of the level passes: node [lo, mid) + [mid, hi) in element positions, and which of
+// its children are large descending runs read backwards (bit 0 left, bit 1 right).
+struct __align__(16) NodeItem {
+  pos_t lo, mid, hi;
+  int32_t rev;
+};
 
 // Launch-argument sentinel: take the work count from the plan header on the device.
 constexpr uint32_t kCountOnDevice = 0xFFFFFFFFu;

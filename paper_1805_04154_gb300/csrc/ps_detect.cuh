@@ -72,7 +72,7 @@ __device__ __forceinline__ Fn unpack_thread_fn(uint32_t w) {
 }
 
 // Largest k with offsets[k] <= p (the segment containing p when segments are non-empty).
-__device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t count, int32_t p) {
+__device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t count, int64_t p) {
   int32_t lo = 0, hi = count;  // offsets[0] = 0 <= p
   while (hi - lo > 1) {
     const int32_t mid = (lo + hi) >> 1;
@@ -103,13 +103,14 @@ __device__ __forceinline__ T chunk_key(const uint4& w, int u) {
 template <class K>
 struct ThreadRuns {
   typedef typename K::T T;
-  int32_t p0, nvalid;  // positions p0 .. p0+nvalid-1 exist
+  int64_t p0;          // first position
+  int32_t nvalid;      // positions p0 .. p0+nvalid-1 exist
   uint64_t L, F, valid;
 
-  __device__ __forceinline__ void load(const T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+  __device__ __forceinline__ void load(const T* __restrict__ keys, int64_t n, const int64_t* __restrict__ offsets,
                                        int32_t count, int32_t tile, int tid) {
-    p0 = tile * kDetectTile + tid * kDetectItems;
-    nvalid = max(0, min(kDetectItems, n - p0));
+    p0 = (int64_t)tile * kDetectTile + tid * kDetectItems;
+    nvalid = (int32_t)max((int64_t)0, min((int64_t)kDetectItems, n - p0));
     valid = (nvalid >= 64) ? ~0ull : ((1ull << nvalid) - 1ull);
     L = 0;
     F = 0;
@@ -148,7 +149,7 @@ struct ThreadRuns {
       int32_t k = segment_of(offsets, count, p0);
       while (k <= count) {
         const int64_t o = offsets[k];
-        if (o > (int64_t)p0 + kDetectItems) break;
+        if (o > p0 + kDetectItems) break;
         if (o >= p0) F |= 1ull << (int)(o - p0);
         ++k;
       }
@@ -165,7 +166,7 @@ struct ThreadRuns {
   // cover eight distinct 16-byte bank groups.  The pairs into the lane's first position and out
   // of its last one use the neighbouring lanes' keys.  A warp whose keys (with the look-ahead)
   // are not wholly inside the array, or whose keys are not 16-byte aligned, takes load().
-  __device__ __forceinline__ void load_staged(const T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+  __device__ __forceinline__ void load_staged(const T* __restrict__ keys, int64_t n, const int64_t* __restrict__ offsets,
                                               int32_t count, int32_t tile, int tid, uint4* __restrict__ stage) {
     static_assert(kDetectItems == 32, "a lane row is 32 keys");
     constexpr int kPerChunk = 16 / (int)sizeof(T);         // keys per 16-byte chunk
@@ -173,7 +174,7 @@ struct ThreadRuns {
     constexpr int kHalves = kRowChunks / 8;                // staged eight chunks per lane at a time
     constexpr int kWarpKeys = 32 * kDetectItems;
     const int lane = tid & 31;
-    const int32_t wp0 = tile * kDetectTile + (tid - lane) * kDetectItems;
+    const int64_t wp0 = (int64_t)tile * kDetectTile + (tid - lane) * kDetectItems;
     if (!(kWarpKeys < n - wp0 && ((uintptr_t)keys & 15u) == 0)) {  // uniform over the warp
       load(keys, n, offsets, count, tile, tid);
       return;
@@ -219,9 +220,9 @@ struct ThreadRuns {
     forced_starts(offsets, count);
   }
   // rebuild the view from the pair / forced-start masks the reduce pass saved
-  __device__ __forceinline__ void restore(int32_t n, int32_t tile, int tid, uint64_t l, uint64_t f) {
-    p0 = tile * kDetectTile + tid * kDetectItems;
-    nvalid = max(0, min(kDetectItems, n - p0));
+  __device__ __forceinline__ void restore(int64_t n, int32_t tile, int tid, uint64_t l, uint64_t f) {
+    p0 = (int64_t)tile * kDetectTile + tid * kDetectItems;
+    nvalid = (int32_t)max((int64_t)0, min((int64_t)kDetectItems, n - p0));
     valid = (nvalid >= 64) ? ~0ull : ((1ull << nvalid) - 1ull);
     L = l;
     F = f;
@@ -279,7 +280,7 @@ struct ThreadRuns {
 // Pass 1: the composed transition function (with run-start counts) of every tile.
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
-detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+detect_reduce_kernel(const typename K::T* __restrict__ keys, int64_t n, const int64_t* __restrict__ offsets,
                      int32_t count, uint64_t* __restrict__ tile_agg, uint64_t* __restrict__ thr_L,
                      uint64_t* __restrict__ thr_F, uint32_t* __restrict__ thr_fn) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
@@ -309,10 +310,11 @@ detect_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const in
 
 // Pass 2 (one CTA of 1024 threads): scan of the tile functions from the START state at
 // position 0.  tile_pre[t] = (state entering tile t) | (run starts before tile t) << 2;
-// hdr->runs = r and S[r] = n.
+// hdr->runs = r and S[r] = n, or kDevTooManyRuns when r exceeds kMaxRuns (kDevInternal if the run
+// arrays' capacity run_cap could not hold r + 1 entries, which the run-length bound excludes).
 static __global__ void __launch_bounds__(1024)
-detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int32_t n, uint64_t* __restrict__ tile_pre,
-                   int32_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
+detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int64_t n, int64_t run_cap,
+                   uint64_t* __restrict__ tile_pre, pos_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
   __shared__ Fn warp_tot[32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t per = (ntiles + 1023) / 1024;
@@ -332,16 +334,22 @@ detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int32_
   Fn wp = fn_identity();
   for (int w = 0; w < warp; ++w) wp = fn_then(wp, warp_tot[w]);
   excl = fn_then(wp, excl);
-  uint32_t state = fn_exit(excl, 0), cnt = fn_cnt(excl, 0);
+  uint32_t state = fn_exit(excl, 0);
+  uint64_t cnt = fn_cnt(excl, 0);  // run counts reach n < 2^32
   for (int32_t t = t0; t < t1; ++t) {
-    tile_pre[t] = (uint64_t)state | ((uint64_t)cnt << 2);
+    tile_pre[t] = (uint64_t)state | (cnt << 2);
     const Fn f = unpack_agg(tile_agg[t]);
     cnt += fn_cnt(f, state);
     state = fn_exit(f, state);
   }
   if (t0 < ntiles && t1 == ntiles) {
-    hdr->runs = (int32_t)cnt;
-    S[cnt] = n;
+    if (cnt > (uint64_t)kMaxRuns || cnt + 1 > (uint64_t)run_cap) {
+      hdr->runs = 0;
+      atomicOr(&hdr->status, (uint32_t)(cnt + 1 > (uint64_t)run_cap ? kDevInternal : kDevTooManyRuns));
+    } else {
+      hdr->runs = (int32_t)cnt;
+      S[cnt] = (pos_t)n;
+    }
   }
 }
 
@@ -349,10 +357,10 @@ detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int32_
 // S[k], directions run_desc[k] and segments run_seg[k] at their global ranks.
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
-detect_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count,
+detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offsets, int32_t count,
                    const uint64_t* __restrict__ tile_pre, const uint64_t* __restrict__ thr_L,
                    const uint64_t* __restrict__ thr_F, const uint32_t* __restrict__ thr_fn,
-                   int32_t* __restrict__ S, uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
+                   pos_t* __restrict__ S, uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
@@ -374,9 +382,10 @@ detect_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count
   excl = fn_then(wp, excl);
   if (tr.nvalid == 0) return;
   const uint64_t pre = tile_pre[blockIdx.x];
-  const uint32_t tile_entry = (uint32_t)(pre & 3u), tile_base = (uint32_t)(pre >> 2);
+  const uint32_t tile_entry = (uint32_t)(pre & 3u);
+  const uint64_t tile_base = pre >> 2;
   const uint32_t entry = fn_exit(excl, tile_entry);  // state at position p0 - 1
-  uint32_t idx = tile_base + fn_cnt(excl, tile_entry);
+  uint64_t idx = tile_base + fn_cnt(excl, tile_entry);
   int pos;
   if (tr.F & 1ull) pos = 0;
   else if (entry == 0) pos = tr.first_start((uint32_t)(tr.L & 1ull));
@@ -384,12 +393,12 @@ detect_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count
   int32_t seg = 0;
   if (offsets != nullptr) seg = segment_of(offsets, count, tr.p0);
   while (pos < tr.nvalid) {
-    const int32_t p = tr.p0 + pos;
+    const int64_t p = tr.p0 + pos;
     if (offsets != nullptr && ((tr.F >> pos) & 1ull)) seg = segment_of(offsets, count, p);
     // descending iff the pair (p, p+1) lies inside the segment and is strictly decreasing
     const bool desc = (p + 1 < n) && !((tr.F >> (pos + 1)) & 1ull) && !((tr.L >> (pos + 1)) & 1ull);
-    if (idx < (uint32_t)n) {  // always true when the tile counts are consistent
-      S[idx] = p;
+    if (idx < (uint64_t)run_cap) {  // always true when the tile counts are consistent
+      S[idx] = (pos_t)p;
       run_desc[idx] = desc ? 1 : 0;
       if (run_seg) run_seg[idx] = seg;
     }

@@ -173,11 +173,11 @@ __device__ __forceinline__ void mr_table(uint64_t Lw, uint64_t Fw, int nvalid, i
 
 // The window of one detection thread: its own pair / forced bits (positions 0..32) and those
 // of the next thread (positions 32..64); positions at or past n are marked forced (a stop).
-__device__ __forceinline__ void mr_window(uint64_t L, uint64_t F, uint64_t Ln, uint64_t Fn, int32_t p0, int32_t n,
+__device__ __forceinline__ void mr_window(uint64_t L, uint64_t F, uint64_t Ln, uint64_t Fn, int64_t p0, int64_t n,
                                           uint64_t& Lw, uint64_t& Fw) {
   Lw = (L & 0xffffffffull) | (Ln << 32);
   Fw = (F & 0xffffffffull) | (Fn << 32);
-  const int64_t left = (int64_t)n - p0;
+  const int64_t left = n - p0;
   if (left < 64) Fw |= ~0ull << (left > 0 ? (int)left : 0);
 }
 
@@ -199,7 +199,7 @@ __device__ __forceinline__ void mr_warp_compose(const uint16_t (*tab)[kMrStates]
 // Pass 1: each tile's table (kMrStates entries); the pair / forced bits are kept for pass 5.
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
-minrun_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const int64_t* __restrict__ offsets,
+minrun_reduce_kernel(const typename K::T* __restrict__ keys, int64_t n, const int64_t* __restrict__ offsets,
                      int32_t count, int w, uint32_t* __restrict__ tile_tab, uint64_t* __restrict__ thr_L,
                      uint64_t* __restrict__ thr_F) {
   __shared__ uint64_t s_L[kDetectThreads], s_F[kDetectThreads];
@@ -219,7 +219,7 @@ minrun_reduce_kernel(const typename K::T* __restrict__ keys, int32_t n, const in
   if (tid + 1 < kDetectThreads) {
     Ln = s_L[tid + 1];
     Fn = s_F[tid + 1];
-  } else if ((int64_t)(blockIdx.x + 1) * kDetectTile < (int64_t)n) {
+  } else if ((int64_t)(blockIdx.x + 1) * kDetectTile < n) {
     ThreadRuns<K> nx;
     nx.load(keys, n, offsets, count, blockIdx.x + 1, 0);
     Ln = nx.L;
@@ -266,20 +266,21 @@ minrun_group_kernel(const uint32_t* __restrict__ tile_tab, int32_t ntiles, int w
 // Pass 3 (one CTA): the groups walked from F(0) at position 0, their tables staged in shared
 // memory kMrTopChunk groups at a time (one coalesced load per chunk instead of a dependent global
 // load per group).  grp_pre[g] = entry state of group g | runs before it << 8; hdr->runs = r and
-// S[r] = n.
+// S[r] = n, or kDevTooManyRuns when r exceeds kMaxRuns.
 constexpr int kMrTopChunk = 64;
 static __global__ void __launch_bounds__(256)
-minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int32_t n, uint64_t* __restrict__ grp_pre,
-                  int32_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
+minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int64_t n, int64_t run_cap,
+                  uint64_t* __restrict__ grp_pre, pos_t* __restrict__ S, PlanHeader* __restrict__ hdr) {
   __shared__ uint32_t s_t[kMrTopChunk * kMrStates];
-  uint32_t st = 0, cnt = 0;  // meaningful in thread 0
+  uint32_t st = 0;  // meaningful in thread 0
+  uint64_t cnt = 0;
   for (int32_t g0 = 0; g0 < ngroups; g0 += kMrTopChunk) {
     const int32_t ng = min(kMrTopChunk, ngroups - g0);
     for (int i = threadIdx.x; i < ng * kMrStates; i += blockDim.x) s_t[i] = grp_tab[(size_t)g0 * kMrStates + i];
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int32_t g = 0; g < ng; ++g) {
-        grp_pre[g0 + g] = (uint64_t)st | ((uint64_t)cnt << 8);
+        grp_pre[g0 + g] = (uint64_t)st | (cnt << 8);
         const uint32_t e = PS_IN_RANGE(st, kMrStates) ? s_t[g * kMrStates + st] : 0u;
         cnt += e >> 6;
         st = e & 63u;
@@ -288,9 +289,16 @@ minrun_top_kernel(const uint32_t* __restrict__ grp_tab, int32_t ngroups, int32_t
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    hdr->runs = (int32_t)cnt;
-    if (cnt <= (uint32_t)n) S[cnt] = n;
-    else post_status(&hdr->status, nullptr, kDevInternal);  // a run has at least one element
+    if (cnt > (uint64_t)kMaxRuns) {
+      hdr->runs = 0;
+      post_status(&hdr->status, nullptr, cnt > (uint64_t)n ? kDevInternal : kDevTooManyRuns);
+    } else if (cnt <= (uint64_t)n && cnt + 1 <= (uint64_t)run_cap) {
+      hdr->runs = (int32_t)cnt;
+      S[cnt] = (pos_t)n;
+    } else {
+      hdr->runs = 0;
+      post_status(&hdr->status, nullptr, kDevInternal);  // a run has at least one element
+    }
   }
 }
 
@@ -320,9 +328,9 @@ minrun_tile_kernel(const uint32_t* __restrict__ tile_tab, int32_t ntiles, const 
 // pair strictly descending, bit 1 extended) and segments run_seg[k].
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
-minrun_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count, int w,
+minrun_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offsets, int32_t count, int w,
                    const uint64_t* __restrict__ tile_pre, const uint64_t* __restrict__ thr_L,
-                   const uint64_t* __restrict__ thr_F, size_t nthreads, int32_t* __restrict__ S,
+                   const uint64_t* __restrict__ thr_F, size_t nthreads, pos_t* __restrict__ S,
                    uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
   __shared__ uint16_t s_tab[kDetectThreads][kMrStates];
   __shared__ uint32_t s_wtab[kDetectThreads / 32][kMrStates];
@@ -367,10 +375,10 @@ minrun_emit_kernel(int32_t n, const int64_t* __restrict__ offsets, int32_t count
   while (pos < tr.nvalid) {
     uint32_t fl;
     const int nx = mr_next(Lw, Fw, pos, w, fl);
-    const int32_t p = tr.p0 + pos;
+    const int64_t p = tr.p0 + pos;
     if (seg && ((tr.F >> pos) & 1ull)) sg = segment_of(offsets, count, p);
-    if (idx < (uint32_t)n) {  // always true when the tables are consistent
-      S[idx] = p;
+    if ((uint64_t)idx < (uint64_t)run_cap) {  // always true when the tables are consistent
+      S[idx] = (pos_t)p;
       run_desc[idx] = (uint8_t)fl;
       if (run_seg) run_seg[idx] = sg;
     }

@@ -21,15 +21,16 @@ struct Ctx {
   int kt = 0;            // key type (powersort.h ps_key_type)
   int key_bytes = 4;
   bool has_vals = false;
-  int32_t n = 0;         // elements (all segments)
+  int64_t n = 0;         // elements (all segments), < kMaxElems
   const int64_t* offsets = nullptr;  // device, count+1 entries, or null for one array
   int32_t count = 1;
 
   void* k[2] = {nullptr, nullptr};   // [0] caller's keys, [1] scratch keys
   uint32_t* v[2] = {nullptr, nullptr};
 
-  // per-run / per-boundary metadata (capacity n + 2)
-  int32_t* S = nullptr;         // run starts, S[r] = n
+  // per-run / per-boundary metadata (run_cap entries: r + 1 <= run_cap)
+  int64_t run_cap = 0;
+  pos_t* S = nullptr;           // run starts, S[r] = n
   uint8_t* run_desc = nullptr;  // run was strictly descending
   int32_t* run_seg = nullptr;   // segment of each run (segmented calls only)
   uint8_t* P = nullptr;         // node power of boundary j (0 for sentinels / segment borders)
@@ -62,9 +63,12 @@ struct Ctx {
   int32_t* small_tasks = nullptr;
   int32_t* leaf_items = nullptr;
   uint32_t* leaf_tile_off = nullptr;
-  int4* level_items = nullptr;         // [kMaxLevels][level_cap]: node (lo, mid, hi, boundary)
+  NodeItem* level_items = nullptr;     // [kMaxLevels][level_cap]: node ranges and reversed children
   uint32_t* level_tile_off = nullptr;
   int32_t level_cap = 0;
+
+  uint32_t poll_limit = kMbarTries;  // bound of every level-pass wait
+  int withhold_depth = -1;      // failure self-test: the level pass of this depth withholds a stage
 
   PlanHeader* hdr = nullptr;
   uint32_t* lib_status = nullptr;  // per-device status word owned by the library

@@ -20,10 +20,10 @@ struct Launch {
     if (c.min_run > 1) return detect_minrun(c);
     detect_reduce_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
         (const T*)c.k[0], c.n, c.offsets, c.count, c.detect_state, c.thr_L, c.thr_F, c.thr_fn);
-    detect_scan_kernel<<<1, 1024, 0, c.stream>>>(c.detect_state, c.detect_tiles, c.n, c.detect_state + c.detect_tiles,
-                                                 c.S, c.hdr);
+    detect_scan_kernel<<<1, 1024, 0, c.stream>>>(c.detect_state, c.detect_tiles, c.n, c.run_cap,
+                                                 c.detect_state + c.detect_tiles, c.S, c.hdr);
     detect_emit_kernel<K><<<c.detect_tiles, kDetectThreads, 0, c.stream>>>(
-        c.n, c.offsets, c.count, c.detect_state + c.detect_tiles, c.thr_L, c.thr_F, c.thr_fn, c.S, c.run_desc,
+        c.n, c.run_cap, c.offsets, c.count, c.detect_state + c.detect_tiles, c.thr_L, c.thr_F, c.thr_fn, c.S, c.run_desc,
         c.run_seg);
     return cudaGetLastError();
   }
@@ -36,9 +36,9 @@ struct Launch {
     minrun_reduce_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>((const T*)c.k[0], c.n, c.offsets, c.count,
                                                                     c.min_run, c.mr_tile_tab, c.thr_L, c.thr_F);
     minrun_group_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.min_run, c.mr_grp_tab);
-    minrun_top_kernel<<<1, 256, 0, c.stream>>>(c.mr_grp_tab, groups, c.n, c.mr_grp_pre, c.S, c.hdr);
+    minrun_top_kernel<<<1, 256, 0, c.stream>>>(c.mr_grp_tab, groups, c.n, c.run_cap, c.mr_grp_pre, c.S, c.hdr);
     minrun_tile_kernel<<<groups, 256, 0, c.stream>>>(c.mr_tile_tab, tiles, c.mr_grp_pre, tile_pre);
-    minrun_emit_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>(c.n, c.offsets, c.count, c.min_run, tile_pre,
+    minrun_emit_kernel<K><<<tiles, kDetectThreads, 0, c.stream>>>(c.n, c.run_cap, c.offsets, c.count, c.min_run, tile_pre,
                                                                   c.thr_L, c.thr_F, nthreads, c.S, c.run_desc,
                                                                   c.run_seg);
     return cudaGetLastError();
@@ -72,7 +72,7 @@ struct Launch {
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     if (ntasks == kCountOnDevice)
       subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 4, kSubThreads, bytes, c.stream>>>(
-          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)(c.n + 2), c.hdr,
+          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.hdr,
           c.lib_status);
     else
       subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
@@ -146,7 +146,8 @@ struct Launch {
                                  : (uint32_t)std::min<uint64_t>(ntiles, (uint64_t)sms * blocks_per_sm);
     level_pass_kernel<K, V, NS, IPT><<<grid, kLevelThreads, bytes, c.stream>>>(
         (const T*)c.k[src], c.v[src], (T*)c.k[dst], c.v[dst], c.level_items + off, c.level_tile_off + off, nitems,
-        ntiles, on_dev ? &c.hdr->level_ctr[depth] : nullptr, (uint32_t)c.level_cap, c.hdr, c.lib_status);
+        ntiles, on_dev ? &c.hdr->level_ctr[depth] : nullptr, (uint32_t)c.level_cap, c.hdr, c.lib_status, c.poll_limit,
+        c.withhold_depth == depth ? 1 : 0);
     return cudaGetLastError();
   }
 

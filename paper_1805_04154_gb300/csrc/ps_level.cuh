@@ -37,34 +37,37 @@ constexpr int kLevelThreads = kMergeThreads + 64;  // 8 consumer warps + issuer 
 constexpr int kQueue = 8;                          // searched tiles the searcher may run ahead
 constexpr int kSearchBatch = 4;                    // tiles searched together (8 lanes each)
 
-// A searched tile: its node (lo, mid, hi, reversed-children flags), outputs [g0, g1), left
-// elements [i0, i1).
+// A searched tile: its node, outputs [g0, g1) (element positions), left-child elements [i0, i1).
 struct QueuedTile {
-  int4 nd;
-  int32_t g0, g1, i0, i1;
+  NodeItem nd;
+  pos_t g0, g1, i0, i1;
 };
 
+// A staged tile as the consumers see it: outputs [g0, g0 + len), la of them from the left child.
 struct StageDesc {
-  int32_t g0, g1, i0, i1;   // outputs [g0, g1); left elements [i0, i1) of the node
-  int32_t lo, mid, la, lb;  // node [lo, mid) + [mid, hi)
-  int32_t aoff, boff, vaoff, vboff;  // smem element offsets of A[i0], B[j0] (keys / payloads)
-  int32_t rev;              // bit 0: the left child is read backwards, bit 1: the right child
-  int32_t pad[3];
+  pos_t g0;
+  int32_t len, la;
+  int32_t aoff, boff, vaoff, vboff;  // smem element offsets of the tile's first left / right element
+  int32_t rev;                       // bit 0: the left child is read backwards, bit 1: the right child
+  int32_t pad[8];
 };
 
 // Position of sorted element i of a node's left / right child: lo + i (mid + i) for a child in
 // order, mid - 1 - i (hi - 1 - i) for a descending run read backwards.  Computed from the node
 // item itself, so the searches keep no extra pointers live.
-__device__ __forceinline__ int32_t left_at(const int4& nd, int32_t i) { return (nd.w & 1) ? nd.y - 1 - i : nd.x + i; }
-__device__ __forceinline__ int32_t right_at(const int4& nd, int32_t j) { return (nd.w & 2) ? nd.z - 1 - j : nd.y + j; }
+__device__ __forceinline__ pos_t left_at(const NodeItem& nd, pos_t i) { return (nd.rev & 1) ? nd.mid - 1 - i : nd.lo + i; }
+__device__ __forceinline__ pos_t right_at(const NodeItem& nd, pos_t j) { return (nd.rev & 2) ? nd.hi - 1 - j : nd.mid + j; }
 
-template <class T>
-struct ChildSeq {  // a child of node nd in the source buffer, indexed in sorted order
-  const T* __restrict__ src;
-  int4 nd;
-  bool right;
-  __device__ __forceinline__ T operator[](int32_t i) const { return src[right ? right_at(nd, i) : left_at(nd, i)]; }
-};
+// Output range of tile k of a node: tiles start at the node's lo and then at the multiples of
+// kTile inside it (the products in 64 bits: a tile's end can pass 2^32 before the min).
+template <int kTile>
+__device__ __forceinline__ pos_t tile_start(const NodeItem& nd, uint32_t k) {
+  return k == 0 ? nd.lo : (pos_t)(((uint64_t)(nd.lo / kTile) + k) * kTile);
+}
+template <int kTile>
+__device__ __forceinline__ pos_t tile_end(const NodeItem& nd, uint32_t k) {
+  return (pos_t)min((uint64_t)nd.hi, ((uint64_t)(nd.lo / kTile) + k + 1) * kTile);
+}
 
 template <class K, bool V, int NS, int IPT>
 struct PassLayout {
@@ -86,19 +89,21 @@ struct PassLayout {
   static constexpr size_t kBytes = kStageOff + NS * kStageBytes;
 };
 
-// smallest i in [a, b] with i == b or A[i] > B[diag-1-i], by a 32-way warp search in global memory
-template <class K, class SA, class SB>
-__device__ __forceinline__ int32_t warp_corank(const SA& A, const SB& B, int32_t diag, int32_t a, int32_t b) {
+// smallest i in [a, b] with i == b or A[i] > B[diag-1-i] (A, B: the node's children in sorted
+// order), by a 32-way warp search in global memory
+template <class K>
+__device__ __forceinline__ pos_t warp_corank(const typename K::T* __restrict__ src, const NodeItem& nd, pos_t diag,
+                                             pos_t a, pos_t b) {
   const int lane = threadIdx.x & 31;
   while (a < b) {
-    const int32_t span = b - a;
-    const int32_t x = a + (int32_t)(((int64_t)span * lane) >> 5);  // probes in [a, b)
-    const bool gt = !key_le<K>(A[x], B[diag - 1 - x]);
+    const pos_t span = b - a;
+    const pos_t x = a + (pos_t)(((uint64_t)span * lane) >> 5);  // probes in [a, b)
+    const bool gt = !key_le<K>(src[left_at(nd, x)], src[right_at(nd, diag - 1 - x)]);
     const uint32_t mask = __ballot_sync(0xffffffffu, gt);
     if (mask) {
       const int fl = __ffs(mask) - 1;
-      const int32_t xf = __shfl_sync(0xffffffffu, x, fl);
-      const int32_t xp = __shfl_sync(0xffffffffu, x, fl > 0 ? fl - 1 : 0);
+      const pos_t xf = __shfl_sync(0xffffffffu, x, fl);
+      const pos_t xp = __shfl_sync(0xffffffffu, x, fl > 0 ? fl - 1 : 0);
       b = xf;
       if (fl > 0) a = xp + 1;
     } else {
@@ -123,18 +128,17 @@ __device__ __forceinline__ bool consumer_all(bool p) {
 // possibly c0 < 0 by a few elements when base itself is not 16-byte aligned).  Empty ranges give
 // an empty chunk.  Needs base aligned to sizeof(E).
 template <class E>
-__device__ __forceinline__ void chunk16(const E* base, int32_t e0, int32_t e1, int32_t& c0, int32_t& c1) {
+__device__ __forceinline__ void chunk16(const E* base, int64_t e0, int64_t e1, int64_t& c0, int64_t& c1) {
   constexpr int kPer = 16 / (int)sizeof(E);
-  const int32_t phase = (int32_t)(((uintptr_t)base & 15u) / sizeof(E));  // elements before base in its block
-  c0 = ((e0 + phase) & ~(kPer - 1)) - phase;
-  // in 64 bits: e1 may lie within a few elements of 2^31
-  c1 = (e1 > e0) ? (int32_t)((((int64_t)e1 + phase + kPer - 1) & ~(int64_t)(kPer - 1)) - phase) : c0;
+  const int64_t phase = (int64_t)(((uintptr_t)base & 15u) / sizeof(E));  // elements before base in its block
+  c0 = ((e0 + phase) & ~(int64_t)(kPer - 1)) - phase;
+  c1 = (e1 > e0) ? (((e1 + phase + kPer - 1) & ~(int64_t)(kPer - 1)) - phase) : c0;
 }
 
-__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool bounded_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
   uint32_t tries = 0;
   while (!mbar_try_wait(bar, parity))
-    if (++tries > kMbarTries) return false;
+    if (++tries > limit) return false;
   return true;
 }
 
@@ -172,7 +176,7 @@ __device__ __forceinline__ void consume_tile(const StageDesc& d, const uint8_t* 
   const T* A = (const T*)stage + d.aoff;
   const T* B = (const T*)stage + d.boff;
   const uint32_t* sv = (const uint32_t*)(stage + Lay::kKeyBytes);
-  const int32_t len = d.g1 - d.g0, la = d.i1 - d.i0, lb = len - la;
+  const int32_t len = d.len, la = d.la, lb = len - la;
   const int32_t diag = tid * IPT;
   if (diag >= len) return;
   int32_t i = corank_serial<K>(A, B, la, lb, diag);
@@ -204,7 +208,7 @@ __device__ __forceinline__ void consume_tile(const StageDesc& d, const uint8_t* 
     for (int q = 0; q < IPT; ++q)
       if (q < cnt) step(q);
   }
-  const int32_t g = d.g0 + diag;
+  const int64_t g = d.g0 + diag;
   if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
     uint4* o = (uint4*)(dstk + g);
 #pragma unroll
@@ -240,9 +244,12 @@ template <class K, bool V, int NS, int IPT>
 __global__ void __launch_bounds__(kLevelThreads, pass_min_blocks(IPT))
 level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __restrict__ srcv,
                   typename K::T* __restrict__ dstk, uint32_t* __restrict__ dstv,
-                  const int4* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
+                  const NodeItem* __restrict__ nodes, const uint32_t* __restrict__ tile_off, uint32_t nitems,
                   uint32_t ntiles, const unsigned long long* __restrict__ ctr, uint32_t cap,
-                  PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+                  PlanHeader* __restrict__ hdr, uint32_t* lib_status, uint32_t polls, int withhold) {
+  // polls: the bound of every wait of the pass (the library default unless a failure self-test
+  // sets a smaller one).  withhold (self-test only): CTA 0's issuer never issues its first tile's
+  // copies, so that stage's "full" barrier is never completed and the waits on it run out.
   typedef typename K::T T;
   typedef PassLayout<K, V, NS, IPT> Lay;
   constexpr int kTile = Lay::kTile;
@@ -253,7 +260,6 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     ntiles = (uint32_t)(v & 0xffffffffull);
     if (nitems > cap) return;  // the plan posted an internal error already
   }
-  constexpr int KU = Lay::KU;
   constexpr int kPassStages = NS;
   extern __shared__ __align__(128) uint8_t smem[];
   uint64_t* full = (uint64_t*)(smem + Lay::kBarOff);
@@ -287,15 +293,12 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     int32_t slot = 0;
     if (lane == 0) slot = slot_of_tile(tile_off, nitems, t_begin);
     slot = __shfl_sync(0xffffffffu, slot, 0);
-    int4 nd = nodes[slot];  // lo, mid, hi, reversed-children flags
-    int32_t la = nd.y - nd.x, lb = nd.z - nd.y;
-    const int32_t k0 = (int32_t)(t_begin - tile_off[slot]);
-    int32_t g0 = (k0 == 0) ? nd.x : (nd.x / kTile + k0) * kTile;
-    int32_t i0 = 0;
-    if (g0 > nd.x) {
-      const int32_t diag = g0 - nd.x;
-      i0 = warp_corank<K>(ChildSeq<T>{srck, nd, false}, ChildSeq<T>{srck, nd, true}, diag, max(0, diag - lb),
-                          min(diag, la));
+    NodeItem nd = nodes[slot];
+    pos_t g0 = tile_start<kTile>(nd, t_begin - tile_off[slot]);
+    pos_t i0 = 0;
+    if (g0 > nd.lo) {
+      const pos_t diag = g0 - nd.lo, lb0 = nd.hi - nd.mid;
+      i0 = warp_corank<K>(srck, nd, diag, diag > lb0 ? diag - lb0 : 0, min(diag, nd.mid - nd.lo));
     }
     // Batches of kSearchBatch tiles: lane group m (8 lanes) finds the end co-rank of the batch's
     // tile m with an 8-way search, all groups at once.  Each window is anchored at the last
@@ -308,12 +311,14 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     uint32_t t = t_begin;
     while (t < t_end && ok) {
       const int nb = (int)min((uint32_t)kSearchBatch, t_end - t);
-      int4 m_nd[kSearchBatch];
-      int32_t m_g0[kSearchBatch], m_g1[kSearchBatch], m_slot[kSearchBatch], m_a[kSearchBatch], m_b[kSearchBatch];
+      NodeItem m_nd[kSearchBatch];
+      pos_t m_g0[kSearchBatch], m_g1[kSearchBatch], m_a[kSearchBatch], m_b[kSearchBatch];
+      int32_t m_slot[kSearchBatch];
       bool m_new[kSearchBatch];
       {
-        int32_t cs = slot, cg0 = g0, ag = g0, ai = i0;
-        int4 cnd = nd;
+        int32_t cs = slot;
+        pos_t cg0 = g0, ag = g0, ai = i0;
+        NodeItem cnd = nd;
 #pragma unroll
         for (int m = 0; m < kSearchBatch; ++m) {
           m_new[m] = false;
@@ -322,29 +327,29 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             if (cs + 1 < (int32_t)nitems && tile_off[cs + 1] <= tt) {
               while (cs + 1 < (int32_t)nitems && tile_off[cs + 1] <= tt) ++cs;
               cnd = nodes[cs];
-              cg0 = cnd.x;
-              ag = cnd.x;
+              cg0 = cnd.lo;
+              ag = cnd.lo;
               ai = 0;
               m_new[m] = true;
             }
-            const int32_t g1 = (int32_t)min((int64_t)cnd.z, ((int64_t)(cg0 / kTile) + 1) * kTile);
-            const int32_t cla = cnd.y - cnd.x, clb = cnd.z - cnd.y, diag = g1 - cnd.x;
+            const pos_t g1 = (pos_t)min((uint64_t)cnd.hi, ((uint64_t)(cg0 / kTile) + 1) * kTile);
+            const pos_t cla = cnd.mid - cnd.lo, clb = cnd.hi - cnd.mid, diag = g1 - cnd.lo;
             m_nd[m] = cnd;
             m_slot[m] = cs;
             m_g0[m] = cg0;
             m_g1[m] = g1;
             // window of the end co-rank (empty window when the tile ends at the node's end)
-            m_a[m] = (g1 < cnd.z) ? max(ai, diag - clb) : cla;
-            m_b[m] = (g1 < cnd.z) ? min(ai + (g1 - ag), cla) : cla;
+            m_a[m] = (g1 < cnd.hi) ? max(ai, diag > clb ? diag - clb : 0) : cla;
+            m_b[m] = (g1 < cnd.hi) ? (pos_t)min((uint64_t)ai + (g1 - ag), (uint64_t)cla) : cla;
             cg0 = g1;
           }
         }
       }
       // group grp searches tile grp (8-way probes)
-      int32_t res = 0;
+      pos_t res = 0;
       {
-        int4 snd = m_nd[0];
-        int32_t sa = m_a[0], sb = m_b[0], sg1 = m_g1[0];
+        NodeItem snd = m_nd[0];
+        pos_t sa = m_a[0], sb = m_b[0], sg1 = m_g1[0];
 #pragma unroll
         for (int m = 1; m < kSearchBatch; ++m)
           if (grp == m) {
@@ -354,17 +359,17 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
             sg1 = m_g1[m];
           }
         if (grp < nb) {
-          const int32_t diag = sg1 - snd.x;
-          int32_t ga = sa, gb = sb;
+          const pos_t diag = sg1 - snd.lo;
+          pos_t ga = sa, gb = sb;
           while (ga < gb) {
-            const int32_t span = gb - ga;
-            const int32_t x = ga + (int32_t)(((int64_t)span * gl) >> 3);
+            const pos_t span = gb - ga;
+            const pos_t x = ga + (pos_t)(((uint64_t)span * gl) >> 3);
             const bool gt = !key_le<K>(srck[left_at(snd, x)], srck[right_at(snd, diag - 1 - x)]);
             const uint32_t msk = (__ballot_sync(gmask, gt) >> (grp * 8)) & 0xFFu;
             if (msk) {
               const int fl = __ffs(msk) - 1;
-              const int32_t xf = __shfl_sync(gmask, x, grp * 8 + fl);
-              const int32_t xp = __shfl_sync(gmask, x, grp * 8 + (fl > 0 ? fl - 1 : 0));
+              const pos_t xf = __shfl_sync(gmask, x, grp * 8 + fl);
+              const pos_t xp = __shfl_sync(gmask, x, grp * 8 + (fl > 0 ? fl - 1 : 0));
               gb = xf;
               if (fl > 0) ga = xp + 1;
             } else {
@@ -374,7 +379,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           res = ga;
         }
       }
-      int32_t m_i1[kSearchBatch];
+      pos_t m_i1[kSearchBatch];
 #pragma unroll
       for (int m = 0; m < kSearchBatch; ++m) m_i1[m] = __shfl_sync(0xffffffffu, res, m * 8);
       // wait for the batch's queue slots, publish the searched tiles
@@ -385,7 +390,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           int good = 1;
           if (lane == 0) {
             good = 0;
-            for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+            for (uint32_t tries = 0; tries < polls; ++tries) {
               if (mbar_try_wait(&qempty[idx % kQueue], ((idx / kQueue) & 1u) ^ 1u)) { good = 1; break; }
               if (*abort_flag) break;
             }
@@ -393,13 +398,13 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           good = __shfl_sync(0xffffffffu, good, 0);
           if (!good) { ok = false; break; }
           if (lane == 0) {
-            const int4 cnd = m_nd[m];
+            const NodeItem cnd = m_nd[m];
             QueuedTile q;
             q.nd = cnd;
             q.g0 = m_g0[m];
             q.g1 = m_g1[m];
             q.i0 = m_new[m] ? 0 : (m == 0 ? i0 : m_i1[m - 1]);
-            q.i1 = (m_g1[m] < cnd.z) ? m_i1[m] : (cnd.y - cnd.x);
+            q.i1 = (m_g1[m] < cnd.hi) ? m_i1[m] : (cnd.mid - cnd.lo);
             queue[idx % kQueue] = q;
             mbar_arrive(&qfull[idx % kQueue]);
           }
@@ -418,9 +423,9 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
           slot = m_slot[m];
           nd = m_nd[m];
           g0 = m_g1[m];
-          i0 = (m_g1[m] < m_nd[m].z) ? m_i1[m] : (m_nd[m].y - m_nd[m].x);
+          i0 = (m_g1[m] < m_nd[m].hi) ? m_i1[m] : (m_nd[m].mid - m_nd[m].lo);
         }
-      if (nb == 1) i0 = (m_g1[0] < m_nd[0].z) ? m_i1[0] : (m_nd[0].y - m_nd[0].x);
+      if (nb == 1) i0 = (m_g1[0] < m_nd[0].hi) ? m_i1[0] : (m_nd[0].mid - m_nd[0].lo);
       t += nb;
     }
     if (!ok && lane == 0) {
@@ -436,7 +441,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     for (; issued < total; ++issued) {
       const uint32_t q = issued % kQueue;
       bool good = false;
-      for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+      for (uint32_t tries = 0; tries < polls; ++tries) {
         if (mbar_try_wait(&qfull[q], (issued / kQueue) & 1u)) { good = true; break; }
         if (*abort_flag) break;
       }
@@ -445,44 +450,38 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       mbar_arrive(&qempty[q]);
       const int s = (int)(issued % kPassStages);
       const uint32_t use = issued / kPassStages;
-      if (!bounded_wait(&empty[s], (use & 1u) ^ 1u)) { ok = false; break; }
-      const int4 cnd = qt.nd;
-      const int32_t cla = cnd.y - cnd.x;
-      const int32_t tg0 = qt.g0, tg1 = qt.g1, ti0 = qt.i0, ti1 = qt.i1;
-      const int32_t tj0 = tg0 - cnd.x - ti0, tj1 = tg1 - cnd.x - ti1;  // right-child elements [tj0, tj1)
-      const bool ra = (cnd.w & 1) != 0, rb = (cnd.w & 2) != 0;
+      if (!bounded_wait(&empty[s], (use & 1u) ^ 1u, polls)) { ok = false; break; }
+      const NodeItem& cnd = qt.nd;
+      const pos_t tj0 = qt.g0 - cnd.lo - qt.i0, tj1 = qt.g1 - cnd.lo - qt.i1;  // right-child elements [tj0, tj1)
+      const bool ra = (cnd.rev & 1) != 0, rb = (cnd.rev & 2) != 0;
       // memory ranges of the tile's sorted elements (a child read backwards has them mirrored
       // at the end of its range)
-      const int32_t a0 = ra ? cnd.y - ti1 : cnd.x + ti0, a1 = ra ? cnd.y - ti0 : cnd.x + ti1;
-      const int32_t b0 = rb ? cnd.z - tj1 : cnd.y + tj0, b1 = rb ? cnd.z - tj0 : cnd.y + tj1;
+      const int64_t a0 = ra ? cnd.mid - qt.i1 : cnd.lo + qt.i0, a1 = ra ? cnd.mid - qt.i0 : cnd.lo + qt.i1;
+      const int64_t b0 = rb ? cnd.hi - tj1 : cnd.mid + tj0, b1 = rb ? cnd.hi - tj0 : cnd.mid + tj1;
       // 16-byte aligned enclosing chunks, computed on absolute addresses (the arrays only need
       // natural alignment; a chunk may start up to 15 bytes before a range and end up to 15
       // bytes after it, always inside 16-byte blocks holding range elements)
-      int32_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
+      int64_t ka0, ka1, kb0, kb1, va0, va1, vb0, vb1;
       chunk16(srck, a0, a1, ka0, ka1);
       chunk16(srck, b0, b1, kb0, kb1);
       chunk16(srcv, a0, a1, va0, va1);
       chunk16(srcv, b0, b1, vb0, vb1);
       StageDesc d;
-      d.g0 = tg0;
-      d.g1 = tg1;
-      d.i0 = ti0;
-      d.i1 = ti1;
-      d.lo = cnd.x;
-      d.mid = cnd.y;
-      d.la = cla;
-      d.lb = cnd.z - cnd.y;
-      d.aoff = a0 - ka0;
-      d.boff = (ka1 - ka0) + (b0 - kb0);
-      d.vaoff = a0 - va0;
-      d.vboff = (va1 - va0) + (b0 - vb0);
-      d.rev = cnd.w & 3;  // the consumers reverse these staged ranges before merging
+      d.g0 = qt.g0;
+      d.len = (int32_t)(qt.g1 - qt.g0);
+      d.la = (int32_t)(qt.i1 - qt.i0);
+      d.aoff = (int32_t)(a0 - ka0);
+      d.boff = (int32_t)((ka1 - ka0) + (b0 - kb0));
+      d.vaoff = (int32_t)(a0 - va0);
+      d.vboff = (int32_t)((va1 - va0) + (b0 - vb0));
+      d.rev = cnd.rev & 3;  // the consumers reverse these staged ranges before merging
       sdesc[s] = d;
       uint8_t* stage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
       T* sk = (T*)stage;
       uint32_t* sv = (uint32_t*)(stage + Lay::kKeyBytes);
       const uint32_t kba = (uint32_t)(ka1 - ka0) * sizeof(T), kbb = (uint32_t)(kb1 - kb0) * sizeof(T);
       const uint32_t vba = V ? (uint32_t)(va1 - va0) * 4u : 0u, vbb = V ? (uint32_t)(vb1 - vb0) * 4u : 0u;
+      if (withhold && blockIdx.x == 0 && issued == 0) continue;  // self-test: this stage never fills
       mbar_arrive_expect_tx(&full[s], kba + kbb + vba + vbb);
       if (kba) bulk_g2s(sk, srck + ka0, kba, &full[s]);
       if (kbb) bulk_g2s(sk + (ka1 - ka0), srck + kb0, kbb, &full[s]);
@@ -498,7 +497,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
     // drain: every copy issued into a stage must have landed before the CTA exits
     for (uint32_t q = (issued > kPassStages ? issued - kPassStages : 0); q < issued; ++q) {
       const int s = (int)(q % kPassStages);
-      bounded_wait(&full[s], (q / kPassStages) & 1u);
+      bounded_wait(&full[s], (q / kPassStages) & 1u, polls);
     }
   } else {
     // ------------------------------ consumers ------------------------------
@@ -508,7 +507,7 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
       const int s = (int)(it % kPassStages);
       const uint32_t use = it / kPassStages;
       bool ready = false;
-      for (uint32_t tries = 0; tries < kMbarTries; ++tries) {
+      for (uint32_t tries = 0; tries < polls; ++tries) {
         if (mbar_try_wait(&full[s], use & 1u)) {
           ready = true;
           break;
@@ -526,9 +525,8 @@ level_pass_kernel(const typename K::T* __restrict__ srck, const uint32_t* __rest
         uint8_t* wstage = smem + Lay::kStageOff + (size_t)s * Lay::kStageBytes;
         T* sk = (T*)wstage;
         uint32_t* svw = (uint32_t*)(wstage + Lay::kKeyBytes);
-        const int32_t la = d.i1 - d.i0, lb = (d.g1 - d.g0) - la;
-        if (d.rev & 1) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.aoff, d.vaoff, la, tid);
-        if (d.rev & 2) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.boff, d.vboff, lb, tid);
+        if (d.rev & 1) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.aoff, d.vaoff, d.la, tid);
+        if (d.rev & 2) reverse_staged<T, V, Lay::KCAP, Lay::VCAP>(sk, svw, d.boff, d.vboff, d.len - d.la, tid);
         consumer_all(true);  // barrier among the consumers: the staged tile is in sorted order
       }
       consume_tile<K, V, IPT, Lay>(d, stage, dstk, dstv, tid);

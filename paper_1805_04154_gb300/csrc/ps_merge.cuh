@@ -136,7 +136,7 @@ __device__ __forceinline__ int32_t sub_corank(const typename E::Arr& X, int32_t 
 }
 
 template <class K, bool V>
-__device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+__device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                                              const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                                              const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
                                              const int32_t task, PlanHeader* __restrict__ hdr,
@@ -176,18 +176,21 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
     if (tid == 0) post_status(&hdr->status, lib_status, kDevInternal);
     return;
   }
-  const int32_t lo = S[L], m = S[R_] - lo, nr = R_ - L;
-  if (m > TS || nr + 1 > RC) {  // cannot happen for a greedy run partition; never overrun SMEM
+  const int64_t lo = S[L];
+  const int64_t m64 = (int64_t)S[R_] - lo;
+  const int32_t nr = R_ - L;
+  if (m64 > TS || nr + 1 > RC) {  // cannot happen for a greedy run partition; never overrun SMEM
     if (tid == 0) post_status(&hdr->status, lib_status, kDevInternal);
     return;
   }
+  const int32_t m = (int32_t)m64;  // the task's elements (at most TS)
 
   // 1. run starts and directions; the keys, tagged with their positions
   int16_t* rs = (int16_t*)meta;
   uint8_t* rdsc = (uint8_t*)(rs + RC);
   bool any_desc = false, any_ext = false;
   for (int32_t k = tid; k <= nr; k += kSubThreads) {
-    rs[k] = (int16_t)(S[L + k] - lo);
+    rs[k] = (int16_t)((int64_t)S[L + k] - lo);
     if (k < nr) {
       rdsc[k] = run_desc[L + k];
       any_desc |= rdsc[k] == 1;
@@ -323,8 +326,8 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
     if (k < w1) {
       const int32_t j = L + k;
       const int32_t at = s_cnt[warp][rd] + __popc(peers & lt_mask);
-      const uint32_t nlo = (uint32_t)(S[nodeL[j]] - lo), nmid = (uint32_t)(S[j] - lo);
-      const uint32_t nhi = (uint32_t)(S[nodeR[j]] - lo);
+      const uint32_t nlo = (uint32_t)((int64_t)S[nodeL[j]] - lo), nmid = (uint32_t)((int64_t)S[j] - lo);
+      const uint32_t nhi = (uint32_t)((int64_t)S[nodeR[j]] - lo);
       if (PS_IN_RANGE(at, RC)) ent[at] = (uint64_t)(nlo | (nmid << 16)) | ((uint64_t)nhi << 32);
     }
     __syncwarp();
@@ -436,7 +439,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const int32_t* __restrict
 // One CTA per task (the count known on the host).
 template <class K, bool V>
 __global__ void __launch_bounds__(kSubThreads, 4)
-subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+subtree_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
                const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
@@ -447,7 +450,7 @@ subtree_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restric
 // loop state costs registers, so it is sized for 3 CTAs per SM.
 template <class K, bool V>
 __global__ void __launch_bounds__(kSubThreads, 4)
-subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+subtree_persistent_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                           const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                           const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
                           const int32_t* __restrict__ tasks, uint32_t cap, PlanHeader* __restrict__ hdr,
@@ -467,68 +470,76 @@ subtree_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t
 // first tile once and walks the leaf list from there.
 // ---------------------------------------------------------------------------------------
 template <class K, bool V>
-__device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+__device__ __forceinline__ void leaf_place_one(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                                                const uint8_t* __restrict__ ldepth, int32_t i, uint32_t k) {
   typedef typename K::T T;
   constexpr int kPer = kMergeTile / 256;  // elements (or pairs) per thread
-  const int32_t s = S[i], e = S[i + 1];
+  const int64_t s = S[i], e = S[i + 1];
   const bool desc = (run_desc[i] & 1) != 0;  // extended runs (bit 1) are short: never placed here
   const T* __restrict__ k0 = (const T*)buf.k[0];
   const uint32_t* __restrict__ v0 = buf.v[0];
-  // all loads of the thread first (independent, coalesced even when reversed), then the stores
+  // all loads of the thread first (independent, coalesced even when reversed), then the stores;
+  // 64-bit tile bases, 32-bit offsets inside the tile
   T kx[kPer], ky[kPer];
   uint32_t vx[kPer], vy[kPer];
+  const int64_t base = s + (int64_t)k * kMergeTile;
   if (out_buffer(ldepth[i]) == 1) {
-    T* __restrict__ k1 = (T*)buf.k[1];
-    uint32_t* __restrict__ v1 = buf.v[1];
-    const int32_t q0 = s + (int32_t)k * kMergeTile + threadIdx.x;
-    const int32_t q1 = (int32_t)min((int64_t)e, (int64_t)s + ((int64_t)k + 1) * kMergeTile);
+    // copy to the scratch buffer; element off of the tile comes from base + off, or from its
+    // mirror s + e - 1 - (base + off) when the run is descending
+    T* __restrict__ k1 = (T*)buf.k[1] + base;
+    uint32_t* __restrict__ v1 = buf.v[1] + base;
+    const int32_t cnt = (int32_t)min((int64_t)kMergeTile, e - base);
+    const int64_t from = desc ? s + e - 1 - base : base;
+    const T* __restrict__ ks = k0 + from;
+    const uint32_t* __restrict__ vs = v0 + from;
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int32_t q = q0 + u * 256;
-      if (q < q1) {
-        const int32_t src = desc ? s + e - 1 - q : q;
-        kx[u] = k0[src];
-        if (V) vx[u] = v0[src];
+      const int32_t off = (int32_t)threadIdx.x + u * 256;
+      if (off < cnt) {
+        const int32_t src = desc ? -off : off;
+        kx[u] = ks[src];
+        if (V) vx[u] = vs[src];
       }
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int32_t q = q0 + u * 256;
-      if (q < q1) {
-        k1[q] = kx[u];
-        if (V) v1[q] = vx[u];
+      const int32_t off = (int32_t)threadIdx.x + u * 256;
+      if (off < cnt) {
+        k1[off] = kx[u];
+        if (V) v1[off] = vx[u];
       }
     }
   } else {
-    T* kk = (T*)buf.k[0];
-    uint32_t* vv = buf.v[0];
-    const int32_t half = (e - s) / 2;
-    const int32_t p0 = s + (int32_t)k * kMergeTile + threadIdx.x;
-    const int32_t p1 = (int32_t)min((int64_t)s + half, (int64_t)s + ((int64_t)k + 1) * kMergeTile);
+    // a descending run that is a whole segment: reversed in place, pairs (p, s + e - 1 - p) for p
+    // in the first half; the tile holds p = base + off, its partner is mirror - off
+    T* __restrict__ kk = (T*)buf.k[0];
+    uint32_t* __restrict__ vv = buf.v[0];
+    const int32_t cnt = (int32_t)min((int64_t)kMergeTile, s + (e - s) / 2 - base);
+    T* __restrict__ klo = kk + base;
+    T* __restrict__ khi = kk + (s + e - 1 - base);
+    uint32_t* __restrict__ vlo = vv + base;
+    uint32_t* __restrict__ vhi = vv + (s + e - 1 - base);
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int32_t p = p0 + u * 256;
-      if (p < p1) {
-        const int32_t q = s + e - 1 - p;
-        kx[u] = kk[p];
-        ky[u] = kk[q];
+      const int32_t off = (int32_t)threadIdx.x + u * 256;
+      if (off < cnt) {
+        kx[u] = klo[off];
+        ky[u] = khi[-off];
         if (V) {
-          vx[u] = vv[p];
-          vy[u] = vv[q];
+          vx[u] = vlo[off];
+          vy[u] = vhi[-off];
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int32_t p = p0 + u * 256;
-      if (p < p1) {
-        const int32_t q = s + e - 1 - p;
-        kk[p] = ky[u];
-        kk[q] = kx[u];
+      const int32_t off = (int32_t)threadIdx.x + u * 256;
+      if (off < cnt) {
+        klo[off] = ky[u];
+        khi[-off] = kx[u];
         if (V) {
-          vv[p] = vy[u];
-          vv[q] = vx[u];
+          vlo[off] = vy[u];
+          vhi[-off] = vx[u];
         }
       }
     }
@@ -538,7 +549,7 @@ __device__ __forceinline__ void leaf_place_one(Bufs buf, const int32_t* __restri
 // Tiles [t_begin, t_end) of the leaf list (items[slot] = leaf, its first tile tile_off[slot]).
 // Tiles touch disjoint elements, so the threads need no barrier between tiles.
 template <class K, bool V>
-__device__ __forceinline__ void leaf_place_range(Bufs buf, const int32_t* __restrict__ S,
+__device__ __forceinline__ void leaf_place_range(Bufs buf, const pos_t* __restrict__ S,
                                                  const uint8_t* __restrict__ run_desc,
                                                  const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                                                  const uint32_t* __restrict__ tile_off, uint32_t nitems,
@@ -556,10 +567,15 @@ __device__ __forceinline__ void leaf_place_range(Bufs buf, const int32_t* __rest
   }
 }
 
+// CTAs per SM the placement kernels keep resident (their registers hold a thread's whole share
+// of a tile: 12 keys and payloads, or pairs of them).
+template <class K>
+__host__ __device__ constexpr int leaf_place_min_blocks() { return sizeof(typename K::T) == 4 ? 3 : 2; }
+
 // Grid over the counts known on the host: CTA b owns tiles [b*T/G, (b+1)*T/G).
 template <class K, bool V>
-__global__ void __launch_bounds__(256)
-leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+__global__ void __launch_bounds__(256, leaf_place_min_blocks<K>())
+leaf_place_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                   const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                   const uint32_t* __restrict__ tile_off, uint32_t nitems, uint32_t ntiles,
                   const PlanHeader* __restrict__ hdr) {
@@ -570,8 +586,8 @@ leaf_place_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __rest
 
 // The same over the counts the plan left on the device (no host round trip).
 template <class K, bool V>
-__global__ void __launch_bounds__(256)
-leaf_place_persistent_kernel(Bufs buf, const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+__global__ void __launch_bounds__(256, leaf_place_min_blocks<K>())
+leaf_place_persistent_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                              const uint8_t* __restrict__ ldepth, const int32_t* __restrict__ items,
                              const uint32_t* __restrict__ tile_off, uint32_t cap,
                              const PlanHeader* __restrict__ hdr) {

@@ -11,27 +11,34 @@ namespace ps {
 // Boundary j (1 <= j <= r-1) separates run j-1 = [S[j-1], S[j]) and run j = [S[j], S[j+1]).
 // With positions relative to the segment start and ns the segment length, the normalised
 // midpoints are a = (S[j-1]+S[j]) / (2 ns) and b = (S[j]+S[j+1]) / (2 ns); the power is the
-// index of their first differing fractional bit.  Since ns < 2^31, b - a >= 1/ns > 2^-31, so
-// the first 31 fractional bits decide it: x = floor(a 2^31), y = floor(b 2^31) (< 2^31), and
-// the power is the number of leading zeros of x ^ y in 32 bits.  Boundaries between segments
-// and the sentinels j = 0, j = r get power 0 (smaller than every real power).
+// index of their first differing fractional bit.  The first 31 fractional bits decide it for
+// every ns < 2^32: b - a = (L_{j-1} + L_j) / (2 ns), and a greedy run is at least two elements
+// long unless it is its segment's last, so either L_{j-1} + L_j >= 4 (then b - a >= 2^-31) or the
+// boundary is the segment's last one with lengths (>= 2, 1), where (a, b] = (1 - 5/(2 ns),
+// 1 - 1/ns] contains 1 - 2^-31 whenever ns > 2^31.  So x = floor(a 2^31), y = floor(b 2^31)
+// (< 2^31) differ and the power is the number of leading zeros of x ^ y in 32 bits (<= 31).
+// Boundaries between segments and the sentinels j = 0, j = r get power 0 (smaller than every
+// real power).
 // ---------------------------------------------------------------------------------------
-// floor(a / d) for a < 2^63 and 2 <= d < 2^33, given m = floor((2^64 - 1) / d): division by an
-// invariant integer through a multiply-high (Granlund and Montgomery, PLDI 1994).  Because
-// a m / 2^64 lies in (a/d - 3/4, a/d], the estimate is q or q - 1, fixed by one remainder test.
+// floor(a / d) for a < 2^64 and 2 <= d < 2^33, given m = floor((2^64 - 1) / d): division by an
+// invariant integer through a multiply-high (Granlund and Montgomery, PLDI 1994).  a m / 2^64
+// lies in (a/d - 2, a/d], so the estimate is q, q - 1 or q - 2, fixed by remainder tests (the
+// remainder below 3d < 2^35 is exact in 64-bit wrapping arithmetic).
 __device__ __forceinline__ uint64_t div_invariant(uint64_t a, uint64_t d, uint64_t m) {
   uint64_t q = __umul64hi(a, m);
+  if (a - q * d >= d) ++q;
   if (a - q * d >= d) ++q;
   return q;
 }
 
-__global__ void node_power_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ run_seg,
-                                  const int64_t* __restrict__ offsets, int32_t n, uint8_t* __restrict__ P,
-                                  const PlanHeader* __restrict__ hdr) {
+__global__ void __launch_bounds__(256, 8) node_power_kernel(const pos_t* __restrict__ S, const int32_t* __restrict__ run_seg,
+                                  const int64_t* __restrict__ offsets, int64_t n, uint8_t* __restrict__ P,
+                                  PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   int32_t cached_seg = -1;
   int64_t base = 0, ns = n;
-  uint64_t two_n = 2 * (uint64_t)n, m = ~0ull / (2 * (uint64_t)max(n, 1));
+  uint64_t two_n = 2 * (uint64_t)n, m = ~0ull / (2 * (uint64_t)max(n, (int64_t)1));
+  bool bad = false;
   for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= r; j += gridDim.x * blockDim.x) {
     uint8_t p = 0;
     if (j >= 1 && j < r) {
@@ -53,11 +60,13 @@ __global__ void node_power_kernel(const int32_t* __restrict__ S, const int32_t* 
         const uint64_t r2 = (uint64_t)((int64_t)S[j] + S[j + 1] - 2 * base);
         const uint32_t x = (uint32_t)div_invariant(l2 << 31, two_n, m);
         const uint32_t y = (uint32_t)div_invariant(r2 << 31, two_n, m);
-        p = (uint8_t)min(__clz(x ^ y), 31);
+        bad |= x == y;  // excluded by the run-length argument above
+        p = (uint8_t)__clz(x ^ y);
       }
     }
     P[j] = p;
   }
+  if (bad) post_status(&hdr->status, nullptr, kDevInternal);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -321,7 +330,7 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
 // parent is then the larger-P of its two boundaries and a node's parent the larger-P of its
 // range ends, the same rule as for node powers.
 // ---------------------------------------------------------------------------------------
-__global__ void peek_init_kernel(const int32_t* __restrict__ S, const int32_t* __restrict__ run_seg,
+__global__ void __launch_bounds__(256, 8) peek_init_kernel(const pos_t* __restrict__ S, const int32_t* __restrict__ run_seg,
                                  const int64_t* __restrict__ offsets, uint8_t* __restrict__ P,
                                  int2* __restrict__ front0, uint32_t* __restrict__ count,
                                  const PlanHeader* __restrict__ hdr) {
@@ -339,7 +348,7 @@ __global__ void peek_init_kernel(const int32_t* __restrict__ S, const int32_t* _
       int32_t lo = j, hi = r;  // first run index at or past the segment's end
       while (lo < hi) {
         const int32_t mid = (lo + hi) >> 1;
-        if ((int64_t)S[mid] < end) lo = mid + 1;
+        if (S[mid] < end) lo = mid + 1;
         else hi = mid;
       }
       if (lo - j >= 2) front0[atomicAdd(&count[0], 1u)] = make_int2(j, lo);
@@ -347,7 +356,7 @@ __global__ void peek_init_kernel(const int32_t* __restrict__ S, const int32_t* _
   }
 }
 
-__global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, const int2* __restrict__ cur,
+__global__ void __launch_bounds__(256, 8) peek_level_kernel(const pos_t* __restrict__ S, int level, const int2* __restrict__ cur,
                                   int2* __restrict__ next, uint32_t* __restrict__ count, int32_t cap,
                                   uint8_t* __restrict__ P, int32_t* __restrict__ nodeL, int32_t* __restrict__ nodeR,
                                   uint8_t* __restrict__ ndepth, PlanHeader* __restrict__ hdr) {
@@ -371,7 +380,7 @@ __global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, cons
       int32_t lo = a + 1, hi = b - 1;  // run k containing m: largest k with S[k] <= m
       while (hi - lo > 0) {
         const int32_t mid = (lo + hi + 1) >> 1;
-        if ((int64_t)S[mid] <= m) lo = mid;
+        if (S[mid] <= m) lo = mid;
         else hi = mid - 1;
       }
       const int64_t i = S[lo], jj = (int64_t)S[lo + 1] - 1;
@@ -409,18 +418,18 @@ __global__ void peek_level_kernel(const int32_t* __restrict__ S, int level, cons
 // and reads its children from buffer (d+1) mod 2, so every leaf starts in buffer (depth mod 2).
 // M = sum over leaves of depth x length (Sec. 2.3).
 // ---------------------------------------------------------------------------------------
-__global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
+__global__ void __launch_bounds__(256, 8) plan_kernel(const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                             const uint8_t* __restrict__ P, const int32_t* __restrict__ nodeL,
                             const int32_t* __restrict__ nodeR, const uint8_t* __restrict__ ndepth,
                             uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
-                            int4* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
-                            int32_t level_cap, int32_t small_cap, int32_t merge_tile,
+                            NodeItem* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
+                            int32_t level_cap, uint32_t small_cap, int32_t merge_tile,
                             PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
   unsigned long long cost = 0;
   int32_t maxd = 0;
-  auto node_size = [&](int32_t j) -> int32_t { return S[nodeR[j]] - S[nodeL[j]]; };
+  auto node_size = [&](int32_t j) -> pos_t { return S[nodeR[j]] - S[nodeL[j]]; };
   auto node_parent = [&](int32_t j) -> int32_t {
     const int32_t L = nodeL[j], R = nodeR[j];
     const int pl = P[L], pr = P[R];
@@ -435,12 +444,12 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
       const int32_t d = par < 0 ? 0 : ndepth[par] + 1;
       ldepth[x] = (uint8_t)d;
       maxd = max(maxd, d);
-      const int32_t len = S[x + 1] - S[x];
+      const pos_t len = S[x + 1] - S[x];
       cost += (unsigned long long)d * (unsigned long long)len;
       if (len <= sub_lim) {
         if (par < 0 || node_size(par) > sub_lim) {
           const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
-          if (slot < (uint32_t)small_cap) small_tasks[slot] = ~x;  // leaf task
+          if (slot < small_cap) small_tasks[slot] = ~x;  // leaf task
           else post_status(&hdr->status, nullptr, kDevInternal);
           atomicAdd(&hdr->small_elems, (unsigned long long)len);
         }
@@ -453,8 +462,8 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
         // it) is reversed in place
         uint32_t tiles = 0;
         const bool odd_buf = out_buffer(d) == 1;
-        if (odd_buf) tiles = (uint32_t)(((int64_t)len + kMergeTile - 1) / kMergeTile);
-        else if (desc && d == 0) tiles = (uint32_t)(((int64_t)len / 2 + kMergeTile - 1) / kMergeTile);
+        if (odd_buf) tiles = len / kMergeTile + (len % kMergeTile != 0 ? 1u : 0u);
+        else if (desc && d == 0) tiles = (len / 2) / kMergeTile + ((len / 2) % kMergeTile != 0 ? 1u : 0u);
         if (tiles) {
           const unsigned long long old = atomicAdd(&hdr->leaf_ctr, (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
@@ -470,20 +479,20 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
     }
     // node x (boundary between runs x-1 and x)
     if (x >= 1 && P[x] >= 1) {
-      const int32_t lo = S[nodeL[x]], hi = S[nodeR[x]];
-      const int32_t size = hi - lo;
+      const pos_t lo = S[nodeL[x]], hi = S[nodeR[x]];
+      const pos_t size = hi - lo;
       const int32_t par = node_parent(x);
       if (size <= sub_lim) {
         if (par < 0 || node_size(par) > sub_lim) {
           const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
-          if (slot < (uint32_t)small_cap) small_tasks[slot] = x;
+          if (slot < small_cap) small_tasks[slot] = x;
           else post_status(&hdr->status, nullptr, kDevInternal);
           atomicAdd(&hdr->small_elems, (unsigned long long)size);
         }
       } else {
         const int d = ndepth[x];
         // output tiles: from lo to the next multiple of merge_tile, then whole tiles
-        const uint32_t tiles = (uint32_t)((hi - 1) / merge_tile - lo / merge_tile + 1);
+        const uint32_t tiles = (hi - 1) / (uint32_t)merge_tile - lo / (uint32_t)merge_tile + 1;
         if (d >= kMaxLevels) {
           post_status(&hdr->status, nullptr, kDevInternal);
         } else {
@@ -497,7 +506,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
           const unsigned long long old = atomicAdd(&hdr->level_ctr[d], (1ull << 32) | tiles);
           const uint32_t slot = (uint32_t)(old >> 32);
           if (slot < (uint32_t)level_cap) {
-            level_items[(size_t)d * level_cap + slot] = make_int4(lo, S[x], hi, rev);
+            level_items[(size_t)d * level_cap + slot] = NodeItem{lo, S[x], hi, rev};
             level_tile_off[(size_t)d * level_cap + slot] = (uint32_t)(old & 0xffffffffu);
             atomicAdd(&hdr->level_elems[d], (unsigned long long)size);
           } else {
@@ -532,7 +541,7 @@ __global__ void plan_kernel(const int32_t* __restrict__ S, const uint8_t* __rest
 
 // Sum over runs of L * log2(L) and per-segment n * log2(n) pieces for the entropy statistic:
 // n H = sum_segments n_s lg n_s - sum_runs L lg L.  (Statistic only; not on the sort path.)
-__global__ void entropy_kernel(const int32_t* __restrict__ S, const PlanHeader* __restrict__ hdr, double* out) {
+__global__ void entropy_kernel(const pos_t* __restrict__ S, const PlanHeader* __restrict__ hdr, double* out) {
   const int32_t r = hdr->runs;
   double acc = 0.0;
   for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < r; i += gridDim.x * blockDim.x) {
@@ -568,6 +577,8 @@ __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int32_
 // ---------------------------------------------------------------------------------------
 // Host launchers for the key-independent stages.
 // ---------------------------------------------------------------------------------------
+// Grid of per_sm resident CTAs per SM (the kernels launched with 8 per SM are bounded to 32
+// registers, so all of them are resident at once).
 static int persistent_blocks(int per_sm) {
   static int sms = 0;
   if (sms == 0) {
@@ -582,7 +593,7 @@ static int persistent_blocks(int per_sm) {
 // Peeksort tree levels launched: one per node depth the plan can hold (0 .. kMaxLevels-1) plus
 // one more, whose ranges (a tree deeper than the plan's per-depth lists) post an internal error.
 // Launches past the tree's height find no ranges and return at once.
-static int peek_levels(int32_t) { return kMaxLevels + 1; }
+static int peek_levels(int64_t) { return kMaxLevels + 1; }
 
 static cudaError_t launch_peek_tree(const Ctx& c) {
   const int grid = persistent_blocks(8);
@@ -606,7 +617,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     if (e != cudaSuccess) return e;
     plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                             c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
-                                            c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.merge_tile,
+                                            c.level_items, c.level_tile_off, c.level_cap, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.merge_tile,
                                             c.hdr);
     return cudaGetLastError();
   }
@@ -628,7 +639,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
                                           c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
-                                          c.level_items, c.level_tile_off, c.level_cap, c.n + 2, c.merge_tile,
+                                          c.level_items, c.level_tile_off, c.level_cap, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.merge_tile,
                                           c.hdr);
   return cudaGetLastError();
 }

@@ -58,7 +58,11 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ps_sort_ws(0, ctypes.c_void_p(4098), None, 10, ws, 1 << 20, None) == 1  # int32 needs 4 B
     assert lib.ps_sort_ws(2, ctypes.c_void_p(4100), None, 10, ws, 1 << 20, None) == 1  # uint64 needs 8 B
     assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), ctypes.c_void_p(4106), 10, ws, 1 << 20, None) == 1
-    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1 << 31, ws, 1 << 20, None) == 2
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1 << 32, ws, 1 << 20, None) == 2
+    # n = 2^31 is accepted (64-bit positions); a workspace of 1 MiB is refused as too small
+    assert lib.ps_sort_ws(0, ctypes.c_void_p(4096), None, 1 << 31, ws, 1 << 20, None) == 3
+    # a single array needs run arrays for n/2 + 3 runs, a segmented one for n + 2
+    assert lib.ps_workspace_size(0, 1, 1 << 31, 0) < lib.ps_workspace_size(0, 1, 1 << 31, 1)
     assert lib.ps_workspace_size(0, 1, 1000, 0) > 1000 * 8
     assert lib.ps_workspace_size(7, 1, 1000, 0) == 0
     # n = 0 and n = 1 are no-ops

@@ -127,6 +127,30 @@ def test_bounded_wait_timeout_reported_and_device_usable(ps):
     np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
 
 
+def test_level_pass_timeout_reported_and_device_usable(ps):
+    """The production merge kernel's own bounded waits: in the deepest level pass one CTA never
+    issues the copies of its first tile (a stage that never fills), so its consumers' wait runs
+    out after the given number of polls.  The timeout is reported, nothing faults or hangs, and
+    the next sort on the device equals the oracle's."""
+    keys, vals = workloads.runs_i32(1 << 20, seed=8, max_len=40000)
+    ref = oracle.powersort(keys, vals)
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    ws = torch.empty(ps.ps_workspace_size(0, True, keys.size), dtype=torch.uint8, device="cuda")
+    ps.ps_selftest_level_pass_timeout(dk, dv, ws, polls=1 << 10, key_type=0)
+    assert ps.ps_stream_status() == 5  # PS_ERR_TIMEOUT, then cleared
+    assert ps.ps_stream_status() == 0
+    dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+    ps.ps_sort_ws(dk, dv, ws, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+    # an array without any merge large enough for a level pass has no stage to withhold
+    small, _ = workloads.runs_i32(3000, seed=9)
+    with pytest.raises(ps.PowersortError) as e:
+        ps.ps_selftest_level_pass_timeout(torch.from_numpy(small).cuda(), None, ws, key_type=0)
+    assert e.value.status == 2
+
+
 def _check_batch_minrun(ps, arrays, w):
     """All arrays as segments of one minimal-run-length call, against the oracle per array."""
     off = np.zeros(len(arrays) + 1, np.int64)

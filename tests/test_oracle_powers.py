@@ -82,6 +82,30 @@ def test_exact_power_equals_31bit_form_large_n():
         assert oracle.node_power(s1, e1, e2, n) == oracle.node_power_bits(s1, e1, e2, n)
 
 
+def test_31bit_form_exact_for_greedy_boundaries_below_2p32():
+    """For 2^31 <= n < 2^32 the 31-bit form still equals the exact power on every boundary a
+    greedy run partition can produce: two runs of total length >= 4 (b - a >= 2^-31), or the
+    array's last boundary with lengths (>= 2, 1) -- the only place a run of one element occurs.
+    So powers stay <= 31 although the general bound floor(lg n) + 1 is 32."""
+    rng = np.random.default_rng(8)
+    top = []
+    for _ in range(4000):
+        n = int(rng.integers(1 << 31, 1 << 32))
+        l1 = int(rng.integers(2, 8))
+        l2 = int(rng.integers(max(2, 4 - l1), 8))
+        s1 = int(rng.integers(0, n - l1 - l2 + 1))
+        p = oracle.node_power(s1, s1 + l1, s1 + l1 + l2, n)
+        assert p == oracle.node_power_bits(s1, s1 + l1, s1 + l1 + l2, n) <= 31
+        top.append(p)
+        for l1 in (2, 3, 5):  # the last boundary: a run of one element at the end
+            p = oracle.node_power(n - 1 - l1, n - 1, n, n)
+            assert p == oracle.node_power_bits(n - 1 - l1, n - 1, n, n) <= 31
+    assert max(top) == 31  # the largest power of these sizes does occur
+    # the general bound is reached only by two adjacent runs of one element, which greedy runs
+    # never produce
+    assert oracle.node_power((1 << 31) + 1, (1 << 31) + 2, (1 << 31) + 3, (1 << 32) - 1) == 32
+
+
 def test_cartesian_tree_equals_stack_tree_and_monotone_paths():
     rng = np.random.default_rng(11)
     for _ in range(200):
