@@ -193,11 +193,21 @@ def measure_variant(ps, dev, name: str, keys, vals, kt: int, steps: int = 5, tre
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / steps
+    # per-stage device time of one more sort (the library's stage events, outside the timed loop)
+    copies[0][0].copy_(k0)
+    copies[0][1].copy_(v0)
+    torch.cuda.synchronize(dev)
+    ps.ps_profile_enable(True)
+    one(0)
+    torch.cuda.synchronize(dev)
+    stages = {k2: round(v2["ms"], 4) for k2, v2 in ps.ps_profile_read().items() if v2["launches"]}
+    ps.ps_profile_enable(False)
     peak, _ = _peaks()
     ideal = an["cost"] * eb * 2 / (peak * 1e9) * 1e3
     del copies, ws, k0, v0
     return {"workload": name, "n": int(n), "min_run": int(min_run), "runs": int(an["runs"]), "merge_cost": int(an["cost"]),
-            "ms_per_sort": ms, "gkeys_s": n / (ms / 1e3) / 1e9, "merge_cost_roofline_frac": ideal / ms}
+            "ms_per_sort": ms, "gkeys_s": n / (ms / 1e3) / 1e9, "merge_cost_roofline_frac": ideal / ms,
+            "stages_ms": stages}
 
 
 def measure_batched(ps, dev, count: int, reps: int = 3):
@@ -723,9 +733,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving measurement")
     ap.add_argument("--batched-segments", type=int, default=10000)
     ap.add_argument("--serving-requests", type=int, default=300)
-    ap.add_argument("--once", choices=["runs", "perm", "runs_minrun24", "perm_minrun24"], default=None,
-                    help="profiling driver: exactly one sort of the headline (runs) or permutation workload "
-                         "(*_minrun24: runs extended to 24) at --n, no warm-up, no JSON line")
+    ap.add_argument("--once", choices=["runs", "perm", "runs_minrun24", "perm_minrun24", "u64"], default=None,
+                    help="profiling driver: exactly one sort of the headline (runs), permutation or uint64 "
+                         "Pareto(1.2) workload (*_minrun24: runs extended to 24) at --n, no warm-up, no JSON line")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.once:
@@ -745,23 +755,34 @@ def run_once(args):
     import paper_1805_04154_gb300 as ps
     ps.load()
     n = args.n
-    keys, vals = _gen(n, SEED) if args.once.startswith("runs") else workloads.perm_i32(n, seed=SEED)
-    dk = torch.from_numpy(keys).cuda()
+    kt = ps.PS_KEY_I32
+    if args.once == "u64":
+        keys, vals = workloads.pareto_u64(n, seed=SEED, alpha=1.2, distinct=1000, max_len=n // 10)
+        kt = ps.PS_KEY_U64
+        dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    else:
+        keys, vals = _gen(n, SEED) if args.once.startswith("runs") else workloads.perm_i32(n, seed=SEED)
+        dk = torch.from_numpy(keys).cuda()
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
-    ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n), dtype=torch.uint8, device="cuda")
+    orig = dk.clone()
+    ws = torch.empty(ps.ps_workspace_size(kt, True, n), dtype=torch.uint8, device="cuda")
     torch.cuda.synchronize()
     ps.ps_profile_enable(True)
     if args.once.endswith("_minrun24"):
-        ps.ps_sort_minrun_ws(dk, dv, ws, 24, key_type=ps.PS_KEY_I32)
+        ps.ps_sort_minrun_ws(dk, dv, ws, 24, key_type=kt)
     else:
-        ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
+        ps.ps_sort_ws(dk, dv, ws, key_type=kt)
     torch.cuda.synchronize()
     prof = ps.ps_profile_read()
     ps.ps_profile_enable(False)
-    ok = ps.ps_stream_status() == 0 and bool((dk[1:] >= dk[:-1]).all().item())
+    if kt == ps.PS_KEY_U64:  # signed tensor view of unsigned keys: compare in the key order
+        dk, orig = dk ^ (-(1 << 63)), orig ^ (-(1 << 63))
+    ok = ps.ps_stream_status() == 0 and check_sorted_device(dk, dv, orig)
     lp = prof["level_pass"]
+    stages = {k2: round(v2["ms"], 4) for k2, v2 in prof.items() if v2["launches"]}
     print(f"once {args.once} n={n} sorted={ok} level_pass_launches={lp['launches']} "
-          f"level_pass_outputs={lp['bytes'] // 16} config={ps.ps_tune_get(ps.PS_KEY_I32, True)}")
+          f"level_pass_outputs={lp['bytes'] // (2 * (keys.dtype.itemsize + 4))} "
+          f"config={ps.ps_tune_get(kt, True)} stages_ms={stages}")
     return 0 if ok else 1
 
 
