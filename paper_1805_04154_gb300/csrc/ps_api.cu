@@ -59,6 +59,7 @@ size_t carve(Ctx& c, uint8_t* base, int kt, bool vals, int64_t n, bool segmented
   c.nodeR = (int32_t*)take(N * 4);
   c.ndepth = (uint8_t*)take(N);
   c.ldepth = (uint8_t*)take(N);
+  c.micro = (uint8_t*)take(N);
   c.detect_tiles = (int32_t)((n + kDetectTile - 1) / kDetectTile);
   c.detect_state = (uint64_t*)take((size_t)std::max<int32_t>(c.detect_tiles, 1) * 16);  // functions + prefixes
   const size_t dthreads = (size_t)std::max<int32_t>(c.detect_tiles, 1) * kDetectThreads;

@@ -51,6 +51,9 @@ __host__ __device__ constexpr int out_buffer(int d) { return d & 1; }
 // sub_tile(key size) elements is merged completely inside one CTA.
 constexpr int kSubThreads = 256;
 __host__ __device__ constexpr int sub_tile(int key_bytes) { return key_bytes == 8 ? 2048 : 4096; }
+// Inside a task, a subtree of at most micro_tile(key size) elements whose parent is larger (a
+// "micro root") is sorted by one thread in registers instead of level by level.
+__host__ __device__ constexpr int micro_tile(int key_bytes) { return key_bytes == 8 ? 8 : 16; }
 
 // ---------------------------------------------------------------------------------------
 // Key orders.  Every key type is compared through an order-preserving map to an unsigned

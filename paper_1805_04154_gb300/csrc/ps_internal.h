@@ -38,6 +38,7 @@ struct Ctx {
   int32_t* nodeR = nullptr;
   uint8_t* ndepth = nullptr;    // node depth
   uint8_t* ldepth = nullptr;    // leaf depth
+  uint8_t* micro = nullptr;     // 1 for a node that is a micro root (see micro_tile)
 
   uint64_t* detect_state = nullptr;
   int32_t detect_tiles = 0;

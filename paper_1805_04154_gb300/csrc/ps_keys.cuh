@@ -72,11 +72,11 @@ struct Launch {
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
     if (ntasks == kCountOnDevice)
       subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 4, kSubThreads, bytes, c.stream>>>(
-          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.small_tasks, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.hdr,
+          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro, c.small_tasks, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.hdr,
           c.lib_status);
     else
       subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
-                                                                      c.ndepth, c.ldepth, c.small_tasks, c.hdr,
+                                                                      c.ndepth, c.ldepth, c.micro, c.small_tasks, c.hdr,
                                                                       c.lib_status);
     return cudaGetLastError();
   }

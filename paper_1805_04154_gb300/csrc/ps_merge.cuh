@@ -57,6 +57,7 @@ struct SubElem<K, 4> {
   __device__ __forceinline__ static R make(uint32_t key, int32_t pos) {
     return ((uint64_t)K::ord(key) << 32) | (uint32_t)pos;
   }
+  __device__ __forceinline__ static R max_elem() { return ~(R)0; }  // above every element (positions < 2^16)
   // positions differ, so two elements never compare equal
   __device__ __forceinline__ static bool before(R a, R b) { return a < b; }
   __device__ __forceinline__ static bool less(R a, R b) { return a < b; }
@@ -90,6 +91,7 @@ struct SubElem<K, 8> {
     a.p[i] = x.p;
   }
   __device__ __forceinline__ static R make(uint64_t key, int32_t pos) { return R{key, (uint32_t)pos}; }
+  __device__ __forceinline__ static R max_elem() { return R{~0ull, ~0u}; }  // above every element
   // a comes from the left child: it goes first unless its key is greater
   __device__ __forceinline__ static bool before(const R& a, const R& b) { return K::le(a.k, b.k); }
   // the order of (key, position), for elements of one run
@@ -104,6 +106,52 @@ struct SubElem<K, 8> {
 template <class E>
 __device__ __forceinline__ int32_t sub_slot(int32_t p) {
   return p + p / E::IPT;
+}
+
+// Batcher's odd-even merge sort network on N registers (N = 8 or 16): the compare-exchanges of
+// the order of (key, position), listed by the non-recursive form of the construction (for
+// p = 1, 2, 4, ..: for k = p, p/2, .., 1: for j = k mod p, j + 3k, ..: for i < k: compare
+// i + j with i + j + k when both lie in the same block of 2p).  The pairs are compile-time
+// constants, so the values stay in registers.  The network sorts every input: by the 0-1
+// principle it suffices that it sorts all 2^N sequences of zeros and ones, which holds for both
+// sizes (19 and 63 comparators).
+template <int N>
+struct MicroNet;
+template <>
+struct MicroNet<8> {
+  static constexpr int kPairs = 19;
+  __host__ __device__ static constexpr int lo(int c) {
+    constexpr uint8_t t[kPairs] = {0, 2, 4, 6, 0, 1, 4, 5, 1, 5, 0, 1, 2, 3, 2, 3, 1, 3, 5};
+    return t[c];
+  }
+  __host__ __device__ static constexpr int hi(int c) {
+    constexpr uint8_t t[kPairs] = {1, 3, 5, 7, 2, 3, 6, 7, 2, 6, 4, 5, 6, 7, 4, 5, 2, 4, 6};
+    return t[c];
+  }
+};
+template <>
+struct MicroNet<16> {
+  static constexpr int kPairs = 63;
+  __host__ __device__ static constexpr int lo(int c) {
+    constexpr uint8_t t[kPairs] = {0, 2, 4, 6, 8, 10, 12, 14, 0, 1, 4, 5, 8, 9, 12, 13, 1, 5, 9, 13, 0, 1, 2, 3, 8, 9, 10, 11, 2, 3, 10, 11, 1, 3, 5, 9, 11, 13, 0, 1, 2, 3, 4, 5, 6, 7, 4, 5, 6, 7, 2, 3, 6, 7, 10, 11, 1, 3, 5, 7, 9, 11, 13};
+    return t[c];
+  }
+  __host__ __device__ static constexpr int hi(int c) {
+    constexpr uint8_t t[kPairs] = {1, 3, 5, 7, 9, 11, 13, 15, 2, 3, 6, 7, 10, 11, 14, 15, 2, 6, 10, 14, 4, 5, 6, 7, 12, 13, 14, 15, 4, 5, 12, 13, 2, 4, 6, 10, 12, 14, 8, 9, 10, 11, 12, 13, 14, 15, 8, 9, 10, 11, 4, 5, 8, 9, 12, 13, 2, 4, 6, 8, 10, 12, 14};
+    return t[c];
+  }
+};
+
+template <class E, int N>
+__device__ __forceinline__ void micro_sort(typename E::R (&v)[N]) {
+  typedef MicroNet<N> Net;
+#pragma unroll
+  for (int c = 0; c < Net::kPairs; ++c) {
+    const typename E::R a = v[Net::lo(c)], b = v[Net::hi(c)];
+    const bool sw = E::less(b, a);
+    v[Net::lo(c)] = sw ? b : a;
+    v[Net::hi(c)] = sw ? a : b;
+  }
 }
 
 template <class K, bool V>
@@ -139,7 +187,8 @@ template <class K, bool V>
 __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                                              const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                                              const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-                                             const int32_t task, PlanHeader* __restrict__ hdr,
+                                             const uint8_t* __restrict__ micro, const int32_t task,
+                                             PlanHeader* __restrict__ hdr,
                                              uint32_t* lib_status) {
   typedef typename K::T T;
   typedef SubElem<K> E;
@@ -155,6 +204,8 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
   __shared__ int32_t s_lvl[kMaxLevels + 1];  // nodes of relative depth d: entries [s_lvl[d], s_lvl[d+1])
   __shared__ int32_t s_wsum[NW];
   __shared__ int32_t s_maxrd;
+  __shared__ int32_t s_nmicro;
+  constexpr int kMicro = micro_tile((int)sizeof(T));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int32_t runs = hdr->runs;
@@ -204,7 +255,10 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
     if (p < m) E::st(X, sub_slot<E>(p), E::make(gk[lo + p], p));
   }
   for (int t = tid; t < NW * kMaxLevels; t += kSubThreads) (&s_cnt[0][0])[t] = 0;
-  if (tid == 0) s_maxrd = -1;
+  if (tid == 0) {
+    s_maxrd = -1;
+    s_nmicro = 0;
+  }
   const int anyd = __syncthreads_or(any_desc);
   const int anyx = __syncthreads_or(any_ext);
   const int32_t cs = tid * IPT;
@@ -271,16 +325,18 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
       if ((mv >> q) & 1u) E::st(X, sub_slot<E>(cs + q), v[q]);
   }
 
-  // 3. the nodes (boundaries 1..nr-1), sorted by relative depth and by position inside a depth:
-  //    a counting sort over warp chunks (match_any groups a warp's equal depths)
+  // 3. the nodes (boundaries 1..nr-1) larger than kMicro, sorted by relative depth and by
+  //    position inside a depth: a counting sort over warp chunks (match_any groups a warp's equal
+  //    depths).  Nodes of at most kMicro elements lie inside a micro root's subtree (the largest
+  //    such ancestor) and are merged by that root's register sort instead.
   const int32_t chunk = (nr - 1 + NW - 1) / NW;
   const int32_t w0 = 1 + warp * chunk, w1 = min(1 + (warp + 1) * chunk, nr);
   bool bad = false;
   int my_max = -1;
   for (int32_t k0 = w0; k0 < w1; k0 += 32) {
     const int32_t k = k0 + lane;
-    int rd = kMaxLevels;  // lanes past the chunk form their own group
-    if (k < w1) {
+    int rd = kMaxLevels;  // lanes past the chunk and small nodes form their own group
+    if (k < w1 && (int64_t)S[nodeR[L + k]] - (int64_t)S[nodeL[L + k]] > kMicro) {
       rd = (int)ndepth[L + k] - droot;
       if (rd < 0 || rd >= kMaxLevels) {
         bad = true;
@@ -288,7 +344,7 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
       }
     }
     const uint32_t peers = __match_any_sync(0xffffffffu, rd);
-    if (k < w1) {
+    if (rd < kMaxLevels) {
       my_max = max(my_max, rd);
       if (lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
     }
@@ -316,25 +372,55 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
     if (tid == kSubThreads - 1) s_lvl[kMaxLevels] = off + c;
   }
   __syncthreads();
-  uint64_t* ent = (uint64_t*)meta;  // node: lo | mid << 16 | hi << 32 (task-relative)
+  // ent[0 .. ) holds the level nodes: lo | mid << 16 | hi << 32 (task-relative); the micro roots
+  // fill it from the top, lo | hi << 32 (level nodes and micro roots are distinct boundaries)
+  uint64_t* ent = (uint64_t*)meta;
   const unsigned lt_mask = (1u << lane) - 1u;
   for (int32_t k0 = w0; k0 < w1; k0 += 32) {
     const int32_t k = k0 + lane;
     int rd = kMaxLevels;
-    if (k < w1) rd = min(max((int)ndepth[L + k] - droot, 0), kMaxLevels - 1);
-    const uint32_t peers = __match_any_sync(0xffffffffu, rd);
+    uint32_t nlo = 0, nhi = 0;
     if (k < w1) {
       const int32_t j = L + k;
+      nlo = (uint32_t)((int64_t)S[nodeL[j]] - lo);
+      nhi = (uint32_t)((int64_t)S[nodeR[j]] - lo);
+      if ((int32_t)(nhi - nlo) > kMicro) {
+        rd = min(max((int)ndepth[j] - droot, 0), kMaxLevels - 1);
+      } else if (micro[j]) {
+        const int32_t at = RC - 1 - atomicAdd(&s_nmicro, 1);
+        if (PS_IN_RANGE(at, RC)) ent[at] = (uint64_t)nlo | ((uint64_t)nhi << 32);
+      }
+    }
+    const uint32_t peers = __match_any_sync(0xffffffffu, rd);
+    if (rd < kMaxLevels) {
+      const int32_t j = L + k;
       const int32_t at = s_cnt[warp][rd] + __popc(peers & lt_mask);
-      const uint32_t nlo = (uint32_t)((int64_t)S[nodeL[j]] - lo), nmid = (uint32_t)((int64_t)S[j] - lo);
-      const uint32_t nhi = (uint32_t)((int64_t)S[nodeR[j]] - lo);
+      const uint32_t nmid = (uint32_t)((int64_t)S[j] - lo);
       if (PS_IN_RANGE(at, RC)) ent[at] = (uint64_t)(nlo | (nmid << 16)) | ((uint64_t)nhi << 32);
     }
     __syncwarp();
-    if (k < w1 && lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
+    if (rd < kMaxLevels && lane == __ffs(peers) - 1) s_cnt[warp][rd] += __popc(peers);
     __syncwarp();
   }
   __syncthreads();
+
+  // 3b. every micro root's subtree sorted by one thread in registers: its elements in the order of
+  //     (key, position) are exactly the result of its stable merges (left elements first on ties)
+  {
+    const int32_t nmicro = s_nmicro;
+    for (int32_t q = tid; q < nmicro; q += kSubThreads) {
+      const uint64_t e = PS_IN_RANGE(RC - 1 - q, RC) ? ent[RC - 1 - q] : 0ull;
+      const int32_t ml = (int32_t)(e & 0xFFFFu), len = (int32_t)(e >> 32) - ml;
+      R v[kMicro];
+#pragma unroll
+      for (int i = 0; i < kMicro; ++i) v[i] = (i < len) ? E::ld(X, sub_slot<E>(ml + i)) : E::max_elem();
+      micro_sort<E, kMicro>(v);
+#pragma unroll
+      for (int i = 0; i < kMicro; ++i)
+        if (i < len) E::st(X, sub_slot<E>(ml + i), v[i]);
+    }
+    if (nmicro > 0) __syncthreads();  // uniform: s_nmicro is read after a barrier
+  }
 
   // 4. the levels, deepest first
   for (int rd = s_maxrd; rd >= 0; --rd) {
@@ -442,8 +528,9 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-               const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
-  subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[blockIdx.x], hdr, lib_status);
+               const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr,
+               uint32_t* lib_status) {
+  subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, micro, tasks[blockIdx.x], hdr, lib_status);
 }
 
 // A persistent grid over the task count the plan left on the device (no host round trip); the
@@ -453,12 +540,13 @@ __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_persistent_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                           const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                           const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-                          const int32_t* __restrict__ tasks, uint32_t cap, PlanHeader* __restrict__ hdr,
+                          const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, uint32_t cap,
+                          PlanHeader* __restrict__ hdr,
                           uint32_t* lib_status) {
   if (hdr->status & kDevBadOffsets) return;  // nothing moves when the offsets were rejected
   const uint32_t ntasks = min(hdr->n_small, cap);
   for (uint32_t tb = blockIdx.x; tb < ntasks; tb += gridDim.x) {
-    subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, tasks[tb], hdr, lib_status);
+    subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, micro, tasks[tb], hdr, lib_status);
     __syncthreads();  // the next task reuses the shared arrays
   }
 }

@@ -421,7 +421,8 @@ __global__ void __launch_bounds__(256, 8) peek_level_kernel(const pos_t* __restr
 __global__ void __launch_bounds__(256, 8) plan_kernel(const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                             const uint8_t* __restrict__ P, const int32_t* __restrict__ nodeL,
                             const int32_t* __restrict__ nodeR, const uint8_t* __restrict__ ndepth,
-                            uint8_t* __restrict__ ldepth, int32_t sub_lim, int32_t* __restrict__ small_tasks,
+                            uint8_t* __restrict__ ldepth, uint8_t* __restrict__ micro, int32_t sub_lim,
+                            int32_t micro_lim, int32_t* __restrict__ small_tasks,
                             int32_t* __restrict__ leaf_items, uint32_t* __restrict__ leaf_tile_off,
                             NodeItem* __restrict__ level_items, uint32_t* __restrict__ level_tile_off,
                             int32_t level_cap, uint32_t small_cap, int32_t merge_tile,
@@ -482,8 +483,10 @@ __global__ void __launch_bounds__(256, 8) plan_kernel(const pos_t* __restrict__ 
       const pos_t lo = S[nodeL[x]], hi = S[nodeR[x]];
       const pos_t size = hi - lo;
       const int32_t par = node_parent(x);
+      const pos_t psize = par < 0 ? ~(pos_t)0 : node_size(par);
+      micro[x] = (size <= (pos_t)micro_lim && psize > (pos_t)micro_lim) ? 1 : 0;
       if (size <= sub_lim) {
-        if (par < 0 || node_size(par) > sub_lim) {
+        if (psize > (pos_t)sub_lim) {
           const uint32_t slot = atomicAdd(&hdr->n_small, 1u);
           if (slot < small_cap) small_tasks[slot] = x;
           else post_status(&hdr->status, nullptr, kDevInternal);
@@ -615,8 +618,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   if (c.tree == 1) {
     cudaError_t e = launch_peek_tree(c);
     if (e != cudaSuccess) return e;
-    plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
-                                            c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
+    plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro,
+                                            c.sub_lim, micro_tile(c.key_bytes), c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                             c.level_items, c.level_tile_off, c.level_cap, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.merge_tile,
                                             c.hdr);
     return cudaGetLastError();
@@ -637,8 +640,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
   tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
   tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
-  plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth,
-                                          c.sub_lim, c.small_tasks, c.leaf_items, c.leaf_tile_off,
+  plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro,
+                                          c.sub_lim, micro_tile(c.key_bytes), c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                           c.level_items, c.level_tile_off, c.level_cap, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.merge_tile,
                                           c.hdr);
   return cudaGetLastError();
