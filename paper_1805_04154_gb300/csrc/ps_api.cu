@@ -510,7 +510,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   {
     StageTimer t(2, s);
     PS_TRY(kl->small(c, kCountOnDevice));
-    t.done(0, 1);
+    t.done(0, 2);  // the one-task grid and the persistent kernel for any tasks beyond it
   }
   {
     StageTimer t(3, s);

@@ -113,7 +113,7 @@ struct PlanHeader {
   int32_t max_leaf_depth;
   unsigned long long cost;  // merge cost M = sum of leaf depth x run length
   uint32_t n_small;         // subtree-in-SMEM tasks
-  uint32_t pad0;
+  uint32_t small_next;      // device-driven subtree kernel: next task to take (work counter)
   unsigned long long leaf_ctr;               // (count << 32) | tiles of large-leaf placement
   unsigned long long level_ctr[kMaxLevels];  // per depth: (count << 32) | merge tiles
   // element counts for the algorithmic-traffic accounting of stage 4

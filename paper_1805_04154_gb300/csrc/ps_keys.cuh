@@ -3,6 +3,7 @@
 #pragma once
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "ps_detect.cuh"
 #include "ps_detect_minrun.cuh"
@@ -70,14 +71,31 @@ struct Launch {
       attr = true;
     }
     Bufs b{{c.k[0], c.k[1]}, {c.v[0], c.v[1]}};
-    if (ntasks == kCountOnDevice)
+    const uint32_t cap = (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll);
+    if (ntasks == kCountOnDevice) {
+      // one CTA per task up to a bound known without the plan: a small task is a segment's root
+      // or a child of a node larger than the subtree limit, and such nodes are at most about
+      // 2n / limit, so 4n / limit + segments covers every input but pathological trees; the
+      // persistent kernel takes any tasks beyond it (and returns at once otherwise)
+      uint32_t grid = (uint32_t)std::min<int64_t>((int64_t)cap, 4 * c.n / c.sub_lim + (int64_t)c.count + 64);
+      // PS_SUBTREE_GRID (tests only): a smaller one-task grid, so that the persistent kernel
+      // takes the remaining tasks
+      static const uint32_t forced = [] {
+        const char* e = std::getenv("PS_SUBTREE_GRID");
+        return e ? (uint32_t)std::strtoul(e, nullptr, 10) : 0u;
+      }();
+      if (forced) grid = std::min(grid, forced);
+      subtree_kernel<K, V><<<grid, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth,
+                                                                    c.ldepth, c.micro, c.small_tasks, cap, c.hdr,
+                                                                    c.lib_status);
       subtree_persistent_kernel<K, V><<<(uint32_t)sm_count() * 4, kSubThreads, bytes, c.stream>>>(
-          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro, c.small_tasks, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.hdr,
+          b, c.S, c.run_desc, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro, c.small_tasks, grid, cap, c.hdr,
           c.lib_status);
-    else
+    } else {
       subtree_kernel<K, V><<<ntasks, kSubThreads, bytes, c.stream>>>(b, c.S, c.run_desc, c.nodeL, c.nodeR,
-                                                                      c.ndepth, c.ldepth, c.micro, c.small_tasks, c.hdr,
-                                                                      c.lib_status);
+                                                                      c.ndepth, c.ldepth, c.micro, c.small_tasks, 0u,
+                                                                      c.hdr, c.lib_status);
+    }
     return cudaGetLastError();
   }
   static cudaError_t small(const Ctx& c, uint32_t ntasks) {

@@ -522,32 +522,41 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
   }
 }
 
-// One CTA per task (the count known on the host).
+// One CTA per task.  cap != 0: the grid covers the tasks up to a bound that the host computed
+// without the plan (device-driven calls); CTAs past the plan's count return at once.
 template <class K, bool V>
 __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-               const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, PlanHeader* __restrict__ hdr,
-               uint32_t* lib_status) {
+               const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, uint32_t cap,
+               PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
+  if (cap != 0 && ((hdr->status & kDevBadOffsets) || blockIdx.x >= min(hdr->n_small, cap))) return;
   subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, micro, tasks[blockIdx.x], hdr, lib_status);
 }
 
-// A persistent grid over the task count the plan left on the device (no host round trip); the
-// loop state costs registers, so it is sized for 3 CTAs per SM.
+// The tasks past the one-task grid of a device-driven call (tasks first, .. of the plan's count;
+// none for the inputs the grid's bound covers): a persistent grid whose CTAs take tasks from a
+// counter in the plan header.  Its task loop needs far more registers than the one-task kernel
+// (it spills), which is why it only takes what the one-task grid cannot.
 template <class K, bool V>
 __global__ void __launch_bounds__(kSubThreads, 4)
 subtree_persistent_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                           const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                           const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
-                          const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, uint32_t cap,
-                          PlanHeader* __restrict__ hdr,
+                          const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, uint32_t first,
+                          uint32_t cap, PlanHeader* __restrict__ hdr,
                           uint32_t* lib_status) {
   if (hdr->status & kDevBadOffsets) return;  // nothing moves when the offsets were rejected
   const uint32_t ntasks = min(hdr->n_small, cap);
-  for (uint32_t tb = blockIdx.x; tb < ntasks; tb += gridDim.x) {
+  __shared__ uint32_t s_task;
+  for (;;) {
+    if (threadIdx.x == 0) s_task = first + atomicAdd(&hdr->small_next, 1u);
+    __syncthreads();
+    const uint32_t tb = s_task;
+    if (tb >= ntasks) break;  // uniform over the CTA
     subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, micro, tasks[tb], hdr, lib_status);
-    __syncthreads();  // the next task reuses the shared arrays
+    __syncthreads();  // the next task reuses the shared arrays (and s_task)
   }
 }
 

@@ -2,6 +2,8 @@
 launch sized from the plan on the device) against the CPU oracle, its device-side error path,
 and CUDA-graph capture: one captured sort replayed on new inputs in the same buffers gives the
 oracle's result every time (one array and many segments)."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -126,3 +128,43 @@ def test_cuda_graph_segmented_replay(ps):
         ref = oracle.sort_segmented(k2, v2, off)
         np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
         np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
+
+
+CHILD_OVERFLOW = r"""
+import sys
+import numpy as np, torch
+sys.path.insert(0, ROOT)
+import oracle, workloads
+import paper_1805_04154_gb300 as ps
+ps.load()
+keys, vals = workloads.perm_i32(300001, seed=5)
+ref = oracle.powersort(keys, vals)
+dk, dv = torch.from_numpy(keys).cuda(), torch.from_numpy(vals.view(np.int32)).cuda()
+ws = torch.empty(ps.ps_workspace_size(0, True, keys.size), dtype=torch.uint8, device="cuda")
+ps.ps_sort_async_ws(dk, dv, ws, key_type=0)
+assert ps.ps_stream_status() == 0
+assert np.array_equal(dk.cpu().numpy(), ref.keys) and np.array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+k2, v2, off = workloads.segmented_i32(400, seed=6, lo_exp=0, hi_exp=14)
+ref2 = oracle.sort_segmented(k2, v2, off)
+dk, dv = torch.from_numpy(k2).cuda(), torch.from_numpy(v2.view(np.int32)).cuda()
+ws = torch.empty(ps.ps_workspace_size(0, True, k2.size, True), dtype=torch.uint8, device="cuda")
+ps.ps_sort_async_ws(dk, dv, ws, offsets=torch.from_numpy(off).cuda(), key_type=0)
+assert ps.ps_stream_status() == 0
+assert np.array_equal(dk.cpu().numpy(), ref2[0]) and np.array_equal(dv.cpu().numpy().view(np.uint32), ref2[1])
+print("overflow path ok")
+"""
+
+
+def test_device_driven_tasks_beyond_the_one_task_grid():
+    """The device-driven call launches one CTA per subtree task up to a bound the host computes
+    without the plan; tasks beyond it go to a persistent kernel.  A child process caps the
+    one-task grid at 7 CTAs (PS_SUBTREE_GRID, a test setting) so that the persistent kernel
+    takes almost all tasks of a permutation and of a batch of segments; both equal the oracle."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, PS_SUBTREE_GRID="7")
+    r = subprocess.run([sys.executable, "-c", "ROOT = %r\n" % root + CHILD_OVERFLOW], env=env,
+                       capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "overflow path ok" in r.stdout
