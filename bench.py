@@ -222,6 +222,8 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
     v0 = torch.from_numpy(vals.view(np.int32)).to(dev)
     doff = torch.from_numpy(off).to(dev)
     an = ps.ps_analyze(k0, offsets=doff, key_type=ps.PS_KEY_I32)  # merge cost of all segments' trees
+    # the batched mode's own tuned entry (segmented sorts of this size bucket), outside the timing
+    tune = ps.ps_autotune_segmented(k0, v0, doff, key_type=ps.PS_KEY_I32)
     M = int(an["cost"])
     peak, peak_kind = _peaks()
     ideal_ms = M * 8 * 2 / (peak * 1e9) * 1e3
@@ -292,6 +294,8 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
             "merge_cost_roofline": {"M": M, "runs": int(an["runs"]), "bytes": M * 16, "ideal_ms": ideal_ms,
                                     "frac": ideal_ms / batched_ms, "graph_frac": ideal_ms / gbest,
                                     "peak_gbs": peak, "peak_kind": peak_kind},
+            "level_pass_config": {"autotune": tune,
+                                  "in_use": list(ps.ps_tune_get_for(ps.PS_KEY_I32, True, n, True))},
             "batched_entry": "ps_sort_segmented_ws (one call)",
             "graph_entry": "ps_sort_async_ws captured once in a CUDA graph, replayed",
             "plain_entry": "ps_sort_ws per array"}
@@ -334,6 +338,14 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
         plain_one(i)
     plain_busy = time.perf_counter() - t0
     capacity = nreq / plain_busy  # requests per second of back-to-back plain launches
+    # the served mode's own tuned entry: segmented sorts of a batch of the first requests packed
+    # as the server packs them (outside the timing)
+    pk = torch.cat([k for k, _ in reqs[:12]]).to(dev)
+    pv = torch.cat([v for _, v in reqs[:12]]).to(dev)
+    poff = torch.tensor(np.concatenate([[0], np.cumsum([k.numel() for k, _ in reqs[:12]])]), dtype=torch.int64,
+                        device=dev)
+    serve_tune = ps.ps_autotune_segmented(pk, pv, poff, key_type=ps.PS_KEY_F32)
+    del pk, pv, poff
     srv_cfg = dict(budget_bytes=64 << 30, max_batch_keys=1 << 25, slots=3)
     warm = SortServer(ps.PS_KEY_F32, **srv_cfg)
     for i in range(min(4, nreq)):
@@ -343,6 +355,7 @@ def measure_serving(ps, dev, nreq: int, loads=(0.5, 0.8, 1.0, 2.0)):
     out = {"workload": f"{nreq} float32 requests, sizes floor(2^U(10,24)), ~1% NaN/+-0 (totalOrder), "
                        "Pareto(1.5) runs, uint32 payload, Poisson arrivals", "keys": int(total),
            "plain_capacity_req_s": capacity, "plain_back_to_back_gkeys_s": total / plain_busy / 1e9,
+           "level_pass_config": {"autotune": serve_tune, "batch_keys": int(sum(k.numel() for k, _ in reqs[:12]))},
            "merge_cost_roofline": {"M": M, "bytes": M * 16, "ideal_ms": ideal_s * 1e3, "peak_gbs": peak,
                                    "peak_kind": peak_kind, "plain_back_to_back_frac": ideal_s / plain_busy,
                                    "note": "frac = ideal device time of all merges / wall time of the whole "
@@ -538,7 +551,7 @@ def run_gpu(args):
                 tr = json.load(f)
             csrc = os.path.join(ROOT, "paper_1805_04154_gb300", "csrc")
             src = b"".join(open(os.path.join(csrc, f), "rb").read() for f in tr.get("sources", []))
-            cfg = ps.ps_tune_get(ps.PS_KEY_I32, True)
+            cfg = ps.ps_tune_get_for(ps.PS_KEY_I32, True, n)
             same_cfg = list(tr.get("config", [])) == [int(cfg[0]), int(cfg[1])]
             if (src and same_cfg and tr.get("source_sha256") == hashlib.sha256(src).hexdigest()
                     and mt["launches"]):
@@ -567,9 +580,10 @@ def run_gpu(args):
             "plan": {"runs": int(an["runs"]), "merge_cost": int(M), "entropy_bits": H,
                      "max_leaf_depth": int(an["leaf_depth"].max())},
             "stages_ms_per_step": stages_ms, "gpu_launches": int(launches), "clocks": clocks,
-            "level_pass_config": {"items_per_thread": ps.ps_tune_get(ps.PS_KEY_I32, True)[0],
-                                  "stages": ps.ps_tune_get(ps.PS_KEY_I32, True)[1],
-                                  "autotune": tune},
+            "level_pass_config": {"items_per_thread": ps.ps_tune_get_for(ps.PS_KEY_I32, True, n)[0],
+                                  "stages": ps.ps_tune_get_for(ps.PS_KEY_I32, True, n)[1],
+                                  "autotune": tune,
+                                  "entries": {"plain, 2^24 <= n < 2^28 (headline)": tune}},
             "sorted_check": ok}
 
     # end to end through the C ABI with host buffers (pinned), every step H2D + sort + D2H:

@@ -175,8 +175,10 @@ ps_status ps_selftest_level_pass_timeout(int key_type, void* keys, uint32_t* val
 /* Level-pass configuration and its autotuner.  A level pass splits its merges into tiles of
  * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
  * shared-memory buffers; the library carries the configurations (12, 2), (12, 3), (12, 4),
- * (8, 2), (8, 3) and (16, 2).  One configuration per key type and payload choice is used by every
- * later sort on this process (default (8, 2)). */
+ * (8, 2), (8, 3) and (16, 2).  The configuration a sort uses is looked up by key type, payload
+ * choice, plain or segmented call, and the size bucket of its n (n < 2^20, < 2^24, < 2^28, larger):
+ * the tuned entry of that bucket if an autotune call set one, else the default of the key type
+ * and payload choice (ps_tune_set), else (8, 2).  Process-wide. */
 typedef struct {
   int items_per_thread;    /* the chosen configuration */
   int stages;
@@ -187,17 +189,30 @@ typedef struct {
 } ps_tune_result;
 
 /* Time every configuration on copies of the caller's device array keys[0..n) (vals may be NULL;
- * neither is modified; scratch from the library's pool), keep the fastest for this key type and
- * payload choice, and report all timings.  Synchronizes the stream. */
+ * neither is modified; scratch from the library's pool), keep the fastest as the tuned entry of
+ * plain sorts of this key type, payload choice and n's size bucket, and report all timings.
+ * Synchronizes the stream. */
 ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, ps_tune_result* out,
                       void* stream);
 
-/* Set the configuration for a key type and payload choice (0, 0: back to the default);
- * PS_ERR_UNSUPPORTED for a configuration the library does not carry. */
+/* As ps_autotune for segmented sorts: times ps_sort_segmented_ws of the caller's batch (d_offsets:
+ * device int64[count+1] as for ps_sort_segmented_ws) and keeps the fastest as the tuned entry of
+ * segmented sorts of n's size bucket (used by ps_sort_segmented* and by ps_sort_async_ws with
+ * offsets). */
+ps_status ps_autotune_segmented(int key_type, const void* keys, const uint32_t* vals, int64_t n,
+                                const int64_t* d_offsets, int64_t count, ps_tune_result* out, void* stream);
+
+/* Set the default configuration of a key type and payload choice and clear its tuned entries
+ * (0, 0: back to (8, 2)); PS_ERR_UNSUPPORTED for a configuration the library does not carry. */
 ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages);
 
-/* The configuration in use for a key type and payload choice. */
+/* The default configuration of a key type and payload choice (what sorts use in size buckets
+ * without a tuned entry). */
 ps_status ps_tune_get(int key_type, int has_vals, int* items_per_thread, int* stages);
+
+/* The configuration a sort of n elements (segmented != 0: a segmented call) of this key type and
+ * payload choice uses. */
+ps_status ps_tune_get_for(int key_type, int has_vals, int64_t n, int segmented, int* items_per_thread, int* stages);
 
 /* Device-driven sort: as ps_sort_tree_ws (d_offsets NULL, count 1 for one array), but with no
  * host round trip -- every launch after planning takes its work count from the plan on the

@@ -93,6 +93,8 @@ def load():
                 "ps_autotune": ([i32, vp, vp, i64, vp, vp], i32),
                 "ps_tune_set": ([i32, i32, i32, i32], i32),
                 "ps_tune_get": ([i32, i32, vp, vp], i32),
+                "ps_tune_get_for": ([i32, i32, i64, i32, vp, vp], i32),
+                "ps_autotune_segmented": ([i32, vp, vp, i64, vp, i64, vp, vp], i32),
                 "ps_selftest_wait_timeout": ([ctypes.c_uint32, vp], i32),
                 "ps_selftest_level_pass_timeout": ([i32, vp, vp, i64, ctypes.c_uint32, vp, sz, vp], i32),
                 "ps_sort_tree_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
@@ -477,6 +479,31 @@ def ps_autotune(keys: torch.Tensor, vals: torch.Tensor | None = None, key_type: 
     return {"items_per_thread": out.items_per_thread, "stages": out.stages,
             "variants": [{"items_per_thread": out.variant_items[i], "stages": out.variant_stages[i],
                           "ms": out.variant_ms[i]} for i in range(out.n_variants)]}
+
+
+def ps_autotune_segmented(keys: torch.Tensor, vals: torch.Tensor | None, offsets: torch.Tensor,
+                          key_type: int | None = None, stream=None) -> dict:
+    """ps_autotune for segmented batches: times the segmented sort of ``keys``/``vals`` (unchanged)
+    with ``offsets`` and keeps the fastest configuration for segmented sorts of this size."""
+    kt = _key_type(keys, key_type)
+    _check_vals(vals, keys)
+    count = _segments(offsets, keys)
+    out = _Tune()
+    _check(load().ps_autotune_segmented(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), keys.numel(),
+                                        _dev_ptr(offsets, "offsets"), count, ctypes.byref(out),
+                                        _stream_ptr(stream, keys.device)), "ps_autotune_segmented")
+    return {"items_per_thread": out.items_per_thread, "stages": out.stages,
+            "variants": [{"items_per_thread": out.variant_items[i], "stages": out.variant_stages[i],
+                          "ms": out.variant_ms[i]} for i in range(out.n_variants)]}
+
+
+def ps_tune_get_for(key_type: int, has_vals: bool, n: int, segmented: bool = False) -> tuple[int, int]:
+    """The level-pass configuration a sort of n elements uses (tuned entry of its size bucket, else
+    the default)."""
+    a, b = ctypes.c_int(0), ctypes.c_int(0)
+    _check(load().ps_tune_get_for(key_type, 1 if has_vals else 0, int(n), 1 if segmented else 0, ctypes.byref(a),
+                                  ctypes.byref(b)), "ps_tune_get_for")
+    return a.value, b.value
 
 
 def ps_tune_set(key_type: int, has_vals: bool, items_per_thread: int, stages: int) -> None:

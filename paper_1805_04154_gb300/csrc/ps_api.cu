@@ -242,14 +242,21 @@ int default_variant() {
   return v;
 }
 
-std::atomic<int> g_tune[4][2];  // 0 = default
+// Tuned configurations: a default per key type and payload choice (ps_tune_set), and entries per
+// plain / segmented call and size bucket of the call's n (ps_autotune, ps_autotune_segmented),
+// which take precedence.  0 = not set.
+constexpr int kTuneBuckets = 4;
+int tune_bucket(int64_t n) { return n < (1 << 20) ? 0 : n < (1 << 24) ? 1 : n < (1 << 28) ? 2 : 3; }
+std::atomic<int> g_tune[4][2];                       // [key type][payload]
+std::atomic<int> g_tune_bucket[4][2][2][kTuneBuckets];  // [key type][payload][segmented][bucket]
 thread_local int t_variant_override = 0;  // set by the autotuner around its trial sorts
 // Failure self-test (ps_selftest_level_pass_timeout): the poll bound of the level passes and
 // whether the deepest one withholds a stage; set only around that entry point's sort.
 thread_local uint32_t t_selftest_polls = 0;
 
-void apply_pass_config(Ctx& c, int kt, bool vals) {
+void apply_pass_config(Ctx& c, int kt, bool vals, int64_t n, bool segmented) {
   int v = t_variant_override;
+  if (!v) v = g_tune_bucket[kt][vals ? 1 : 0][segmented ? 1 : 0][tune_bucket(n)].load();
   if (!v) v = g_tune[kt][vals ? 1 : 0].load();
   if (!v) v = default_variant();
   c.pass_ipt = v / 16;
@@ -363,7 +370,7 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
   c.min_run = min_run;
-  apply_pass_config(c, kt, vals != nullptr);
+  apply_pass_config(c, kt, vals != nullptr, n, segmented);
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
@@ -487,7 +494,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
   if (!c.lib_status) return PS_ERR_CUDA;
-  apply_pass_config(c, kt, vals != nullptr);
+  apply_pass_config(c, kt, vals != nullptr, n, segmented);
   const KeyLaunch* kl = launch_for(kt);
   // deepest node: depth < power <= floor(lg n) + 1 for Alg. 2; the plan's limit for Alg. 1
   int maxd = kMaxLevels - 1;
@@ -685,30 +692,50 @@ ps_status ps_selftest_level_pass_timeout(int key_type, void* keys, uint32_t* val
 
 ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages) {
   if (!launch_for(key_type)) return PS_ERR_INVALID_ARG;
-  if (items_per_thread == 0 && stages == 0) {  // back to the default
-    g_tune[key_type][has_vals ? 1 : 0].store(0);
+  const int hv = has_vals ? 1 : 0;
+  if (items_per_thread == 0 && stages == 0) {  // back to the default, tuned entries cleared
+    g_tune[key_type][hv].store(0);
+    for (int sg = 0; sg < 2; ++sg)
+      for (int b = 0; b < kTuneBuckets; ++b) g_tune_bucket[key_type][hv][sg][b].store(0);
     return PS_OK;
   }
   if (!known_variant(items_per_thread, stages)) return PS_ERR_UNSUPPORTED;
-  g_tune[key_type][has_vals ? 1 : 0].store(pass_variant(items_per_thread, stages));
+  g_tune[key_type][hv].store(pass_variant(items_per_thread, stages));
+  for (int sg = 0; sg < 2; ++sg)
+    for (int b = 0; b < kTuneBuckets; ++b) g_tune_bucket[key_type][hv][sg][b].store(0);
   return PS_OK;
 }
 
 ps_status ps_tune_get(int key_type, int has_vals, int* items_per_thread, int* stages) {
   if (!launch_for(key_type) || !items_per_thread || !stages) return PS_ERR_INVALID_ARG;
   Ctx c;
-  apply_pass_config(c, key_type, has_vals != 0);
+  apply_pass_config(c, key_type, has_vals != 0, 0, false);
   *items_per_thread = c.pass_ipt;
   *stages = c.pass_stages;
   return PS_OK;
 }
 
-ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, ps_tune_result* out,
-                      void* stream) {
+ps_status ps_tune_get_for(int key_type, int has_vals, int64_t n, int segmented, int* items_per_thread, int* stages) {
+  if (!launch_for(key_type) || !items_per_thread || !stages || n < 0) return PS_ERR_INVALID_ARG;
+  Ctx c;
+  apply_pass_config(c, key_type, has_vals != 0, n, segmented != 0);
+  *items_per_thread = c.pass_ipt;
+  *stages = c.pass_stages;
+  return PS_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Time every level-pass configuration on copies of keys/vals (plain when d_offsets is null, else
+// segmented with the caller's device offsets) and store the fastest for the call's kind and size.
+ps_status autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                   int64_t count, ps_tune_result* out, cudaStream_t s) {
   ps_status st = check_args(key_type, keys, vals, n);
   if (st != PS_OK) return st;
-  if (!out || n < 2) return PS_ERR_INVALID_ARG;
-  cudaStream_t s = (cudaStream_t)stream;
+  const bool seg = d_offsets != nullptr;
+  if (!out || n < 2 || (seg && (count < 1 || count >= ((int64_t)1 << 31)))) return PS_ERR_INVALID_ARG;
   int dev = 0;
   PS_TRY(cudaGetDevice(&dev));
   cudaMemPool_t pool = lib_pool(dev);
@@ -717,7 +744,7 @@ ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int6
   auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
   const size_t kbytes = up((size_t)n * kb + 16), vbytes = vals ? up((size_t)n * 4 + 16) : 0;
   Ctx tmp;
-  const size_t wbytes = carve(tmp, nullptr, key_type, vals != nullptr, n, false);
+  const size_t wbytes = carve(tmp, nullptr, key_type, vals != nullptr, n, seg);
   uint8_t* base = nullptr;
   if (cudaMallocFromPoolAsync((void**)&base, kbytes + vbytes + wbytes, pool, s) != cudaSuccess)
     return PS_ERR_OUT_OF_MEMORY;
@@ -742,7 +769,7 @@ ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int6
         st = cuda_status(e);
         break;
       }
-      st = run(key_type, dk, dv, n, nullptr, 1, false, ws, wbytes, s, nullptr);
+      st = run(key_type, dk, dv, n, d_offsets, seg ? count : 1, seg, ws, wbytes, s, nullptr);
       if (st != PS_OK) break;
       e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -769,10 +796,26 @@ ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int6
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (st != PS_OK) return st;
-  g_tune[key_type][vals ? 1 : 0].store(pass_variant(kPassVariantIpt[best], kPassVariantStages[best]));
+  g_tune_bucket[key_type][vals ? 1 : 0][seg ? 1 : 0][tune_bucket(n)].store(
+      pass_variant(kPassVariantIpt[best], kPassVariantStages[best]));
   out->items_per_thread = kPassVariantIpt[best];
   out->stages = kPassVariantStages[best];
   return PS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ps_status ps_autotune(int key_type, const void* keys, const uint32_t* vals, int64_t n, ps_tune_result* out,
+                      void* stream) {
+  return autotune(key_type, keys, vals, n, nullptr, 1, out, (cudaStream_t)stream);
+}
+
+ps_status ps_autotune_segmented(int key_type, const void* keys, const uint32_t* vals, int64_t n,
+                                const int64_t* d_offsets, int64_t count, ps_tune_result* out, void* stream) {
+  if (!d_offsets) return PS_ERR_INVALID_ARG;
+  return autotune(key_type, keys, vals, n, d_offsets, count, out, (cudaStream_t)stream);
 }
 
 ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
@@ -1050,7 +1093,7 @@ ps_status run_noalloc(int kt, void* keys, uint32_t* vals, int64_t n, cudaStream_
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = (uint32_t*)(scratch + kNoAllocScratchBytes - 256);  // this entry's own status word
-  apply_pass_config(c, kt, vals != nullptr);  // the level-pass configuration every other sort uses
+  apply_pass_config(c, kt, vals != nullptr, n, false);  // the level-pass configuration every other sort uses
   const KeyLaunch* kl = launch_for(kt);
 
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));

@@ -74,10 +74,11 @@ struct Launch {
     const uint32_t cap = (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll);
     if (ntasks == kCountOnDevice) {
       // one CTA per task up to a bound known without the plan: a small task is a segment's root
-      // or a child of a node larger than the subtree limit, and such nodes are at most about
-      // 2n / limit, so 4n / limit + segments covers every input but pathological trees; the
-      // persistent kernel takes any tasks beyond it (and returns at once otherwise)
-      uint32_t grid = (uint32_t)std::min<int64_t>((int64_t)cap, 4 * c.n / c.sub_lim + (int64_t)c.count + 64);
+      // or a child of a node larger than the subtree limit, whose subtrees hold more than half the
+      // limit in balanced parts of the tree, so 2n / limit + segments covers ordinary inputs (a
+      // random permutation has about 1.4n / limit tasks, the 10,000-segment batch 0.2n / limit);
+      // surplus CTAs return at once, and the persistent kernel takes any tasks beyond the bound
+      uint32_t grid = (uint32_t)std::min<int64_t>((int64_t)cap, 2 * c.n / c.sub_lim + (int64_t)c.count + 64);
       // PS_SUBTREE_GRID (tests only): a smaller one-task grid, so that the persistent kernel
       // takes the remaining tasks
       static const uint32_t forced = [] {

@@ -55,9 +55,35 @@ def test_autotune_picks_a_configuration(ps):
     assert all(v["ms"] > 0 for v in res["variants"])
     best = min(res["variants"], key=lambda v: v["ms"])
     assert (res["items_per_thread"], res["stages"]) == (best["items_per_thread"], best["stages"])
-    assert ps.ps_tune_get(0, True) == (res["items_per_thread"], res["stages"])
+    # the tuned entry belongs to plain sorts of this size bucket (2^20 <= n < 2^24)
+    assert ps.ps_tune_get_for(0, True, keys.size) == (res["items_per_thread"], res["stages"])
     assert torch.equal(dk, before_k) and torch.equal(dv, before_v)  # the input is left alone
     ps.ps_sort(dk, dv, key_type=0)
     ref = oracle.powersort(keys, vals)
     np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
     np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+
+
+def test_tuned_entries_by_kind_and_size_bucket(ps):
+    """ps_autotune_segmented times the segmented sort of a batch and keeps its choice for segmented
+    sorts of that size bucket only; ps_tune_set sets the default and clears the tuned entries."""
+    ps.ps_tune_set(0, True, 12, 3)  # a default that differs from the tuned entries below
+    keys, vals, off = workloads.segmented_i32(300, seed=12, lo_exp=8, hi_exp=15)
+    dk = torch.from_numpy(keys).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    doff = torch.from_numpy(off).cuda()
+    res = ps.ps_autotune_segmented(dk, dv, doff, key_type=0)
+    assert len(res["variants"]) == len(VARIANTS)
+    best = min(res["variants"], key=lambda v: v["ms"])
+    choice = (res["items_per_thread"], res["stages"])
+    assert choice == (best["items_per_thread"], best["stages"])
+    assert ps.ps_tune_get_for(0, True, keys.size, segmented=True) == choice
+    assert ps.ps_tune_get_for(0, True, keys.size, segmented=False) == (12, 3)  # plain: the default
+    assert ps.ps_tune_get_for(0, True, 1 << 26, segmented=True) == (12, 3)    # another bucket
+    ref = oracle.sort_segmented(keys, vals, off)
+    ps.ps_sort_segmented(dk, dv, doff, key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
+    ps.ps_tune_set(0, True, 0, 0)
+    assert ps.ps_tune_get_for(0, True, keys.size, segmented=True) == (8, 2)
