@@ -175,10 +175,12 @@ ps_status ps_selftest_level_pass_timeout(int key_type, void* keys, uint32_t* val
 /* Level-pass configuration and its autotuner.  A level pass splits its merges into tiles of
  * items_per_thread x 256 outputs (the merge-path granularity) staged through a ring of `stages`
  * shared-memory buffers; the library carries the configurations (12, 2), (12, 3), (12, 4),
- * (8, 2), (8, 3) and (16, 2).  The configuration a sort uses is looked up by key type, payload
- * choice, plain or segmented call, and the size bucket of its n (n < 2^20, < 2^24, < 2^28, larger):
+ * (8, 2), (8, 3), (16, 2), (6, 2) and (10, 2).  The configuration a sort uses is looked up by key
+ * type, payload choice, plain or segmented call, and the size bucket of its n (n < 2^20, < 2^24,
+ * < 2^28, larger):
  * the tuned entry of that bucket if an autotune call set one, else the default of the key type
- * and payload choice (ps_tune_set), else (8, 2).  Process-wide. */
+ * and payload choice (ps_tune_set), else (8, 2) for 4-byte keys and (6, 2) for 8-byte keys.
+ * Process-wide. */
 typedef struct {
   int items_per_thread;    /* the chosen configuration */
   int stages;
@@ -203,7 +205,7 @@ ps_status ps_autotune_segmented(int key_type, const void* keys, const uint32_t* 
                                 const int64_t* d_offsets, int64_t count, ps_tune_result* out, void* stream);
 
 /* Set the default configuration of a key type and payload choice and clear its tuned entries
- * (0, 0: back to (8, 2)); PS_ERR_UNSUPPORTED for a configuration the library does not carry. */
+ * (0, 0: back to the built-in default); PS_ERR_UNSUPPORTED for a configuration the library does not carry. */
 ps_status ps_tune_set(int key_type, int has_vals, int items_per_thread, int stages);
 
 /* The default configuration of a key type and payload choice (what sorts use in size buckets

@@ -222,9 +222,11 @@ struct AnalyzeOut {
 };
 
 // Level-pass configuration (items per consumer thread, ring stages), per key type and payload
-// choice: 8 items and 2 stages unless PS_PASS_STAGES picks another compiled ring depth for 8
-// items, ps_tune_set or ps_autotune choose otherwise.  Packed as pass_variant(ipt, stages).
-constexpr int kDefaultPassIpt = 8;  // outputs per consumer thread of the default level pass
+// choice: 8 items and 2 stages for 4-byte keys, 6 items and 2 stages for 8-byte keys (measured the
+// fastest on GB300: at 6 items a warp's 8-byte shared-memory reads meet 4-way bank conflicts where
+// 8 items give 16-way ones), unless PS_PASS_STAGES picks another compiled ring depth for that item
+// count, or ps_tune_set or ps_autotune choose otherwise.  Packed as pass_variant(ipt, stages).
+int default_pass_ipt(int key_bytes) { return key_bytes == 8 ? 6 : 8; }
 
 bool known_variant(int ipt, int stages) {
   for (int i = 0; i < kPassVariants; ++i)
@@ -232,14 +234,14 @@ bool known_variant(int ipt, int stages) {
   return false;
 }
 
-int default_variant() {
-  static int v = -1;
-  if (v < 0) {
+int default_variant(int key_bytes) {
+  static int stages = -1;
+  if (stages < 0) {
     const char* e = std::getenv("PS_PASS_STAGES");
-    const int x = e ? std::atoi(e) : 0;
-    v = known_variant(kDefaultPassIpt, x) ? pass_variant(kDefaultPassIpt, x) : pass_variant(kDefaultPassIpt, 2);
+    stages = e ? std::atoi(e) : 2;
   }
-  return v;
+  const int ipt = default_pass_ipt(key_bytes);
+  return known_variant(ipt, stages) ? pass_variant(ipt, stages) : pass_variant(ipt, 2);
 }
 
 // Tuned configurations: a default per key type and payload choice (ps_tune_set), and entries per
@@ -258,7 +260,7 @@ void apply_pass_config(Ctx& c, int kt, bool vals, int64_t n, bool segmented) {
   int v = t_variant_override;
   if (!v) v = g_tune_bucket[kt][vals ? 1 : 0][segmented ? 1 : 0][tune_bucket(n)].load();
   if (!v) v = g_tune[kt][vals ? 1 : 0].load();
-  if (!v) v = default_variant();
+  if (!v) v = default_variant(key_bytes(kt));
   c.pass_ipt = v / 16;
   c.pass_stages = v % 16;
   c.merge_tile = c.pass_ipt * kMergeThreads;

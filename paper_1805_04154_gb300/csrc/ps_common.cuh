@@ -33,9 +33,12 @@ constexpr int kTreeTile = kTreeThreads * kTreeChunk;  // 8192
 // Level-pass configurations (items per consumer thread, shared-memory ring stages) compiled
 // into the library; the tile of a pass is items x kMergeThreads outputs.
 __host__ __device__ constexpr int pass_variant(int ipt, int stages) { return ipt * 16 + stages; }
-constexpr int kPassVariants = 6;
-constexpr int kPassVariantIpt[kPassVariants] = {12, 12, 12, 8, 8, 16};
-constexpr int kPassVariantStages[kPassVariants] = {2, 3, 4, 2, 3, 2};
+constexpr int kPassVariants = 8;
+constexpr int kPassVariantIpt[kPassVariants] = {12, 12, 12, 8, 8, 16, 6, 10};
+constexpr int kPassVariantStages[kPassVariants] = {2, 3, 4, 2, 3, 2, 2, 2};
+// 6 and 10 items: a consumer thread's share of keys is an odd multiple of 8 bytes (4-byte keys:
+// 24 or 40 bytes; 8-byte keys: 48 or 80 bytes), so the shared-memory reads of a warp whose lanes
+// walk one input at lane stride IPT keys spread over more banks than at 8 or 12 items.
 
 // Stage 4 (merge passes over HBM): one CTA produces kMergeTile outputs of one merge.
 constexpr int kMergeThreads = 256;

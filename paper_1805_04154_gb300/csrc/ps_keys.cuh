@@ -180,6 +180,8 @@ struct Launch {
       case pass_variant(8, 2): return merge_vs<V, 2, 8>(c, depth, nitems, ntiles);
       case pass_variant(8, 3): return merge_vs<V, 3, 8>(c, depth, nitems, ntiles);
       case pass_variant(16, 2): return merge_vs<V, 2, 16>(c, depth, nitems, ntiles);
+      case pass_variant(6, 2): return merge_vs<V, 2, 6>(c, depth, nitems, ntiles);
+      case pass_variant(10, 2): return merge_vs<V, 2, 10>(c, depth, nitems, ntiles);
       default: return merge_vs<V, 2, 12>(c, depth, nitems, ntiles);
     }
   }

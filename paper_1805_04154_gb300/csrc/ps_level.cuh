@@ -167,7 +167,8 @@ __device__ __forceinline__ void reverse_staged(T* sk, uint32_t* sv, int32_t off,
 
 // One consumer thread's share of a staged tile: the co-rank of its first output inside shared
 // memory, a serial stable merge of up to IPT outputs (the heads of both inputs kept in
-// registers: one shared-memory key read per output), and 128-bit stores.
+// registers: one shared-memory key read per output), and 16-byte stores (8-byte ones where a
+// thread's share of keys or payloads is an odd multiple of 8 bytes).
 template <class K, bool V, int IPT, class Lay>
 __device__ __forceinline__ void consume_tile(const StageDesc& d, const uint8_t* stage, typename K::T* __restrict__ dstk,
                                              uint32_t* __restrict__ dstv, int tid) {
@@ -209,26 +210,49 @@ __device__ __forceinline__ void consume_tile(const StageDesc& d, const uint8_t* 
       if (q < cnt) step(q);
   }
   const int64_t g = d.g0 + diag;
-  if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
-    uint4* o = (uint4*)(dstk + g);
+  bool stored = false;
+  if constexpr (IPT % KU == 0) {  // a thread's keys fill whole 16-byte stores
+    if (cnt == IPT && ((uintptr_t)(dstk + g) & 15u) == 0) {
+      uint4* o = (uint4*)(dstk + g);
 #pragma unroll
-    for (int q = 0; q < IPT / KU; ++q) {
-      uint4 w;
-      T* wt = (T*)&w;
+      for (int q = 0; q < IPT / KU; ++q) {
+        uint4 w;
+        T* wt = (T*)&w;
 #pragma unroll
-      for (int u = 0; u < KU; ++u) wt[u] = key[q * KU + u];
-      o[q] = w;
+        for (int u = 0; u < KU; ++u) wt[u] = key[q * KU + u];
+        o[q] = w;
+      }
+      stored = true;
     }
-  } else {
+  } else {  // 4-byte keys, 6 or 10 items: 8-byte stores
+    static_assert(IPT % 2 == 0 && sizeof(T) == 4, "a thread's keys fill whole 8-byte stores");
+    if (cnt == IPT && ((uintptr_t)(dstk + g) & 7u) == 0) {
+      uint2* o = (uint2*)(dstk + g);
+#pragma unroll
+      for (int q = 0; q < IPT / 2; ++q) {
+        uint2 w;
+        T* wt = (T*)&w;
+        wt[0] = key[2 * q];
+        wt[1] = key[2 * q + 1];
+        o[q] = w;
+      }
+      stored = true;
+    }
+  }
+  if (!stored) {
 #pragma unroll
     for (int q = 0; q < IPT; ++q)
       if (q < cnt) dstk[g + q] = key[q];
   }
   if (V) {
-    if (cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
+    if (IPT % 4 == 0 && cnt == IPT && ((uintptr_t)(dstv + g) & 15u) == 0) {
       uint4* o = (uint4*)(dstv + g);
 #pragma unroll
       for (int q = 0; q < IPT / 4; ++q) o[q] = make_uint4(val[4 * q], val[4 * q + 1], val[4 * q + 2], val[4 * q + 3]);
+    } else if (IPT % 4 == 2 && cnt == IPT && ((uintptr_t)(dstv + g) & 7u) == 0) {  // 6 or 10 items
+      uint2* o = (uint2*)(dstv + g);
+#pragma unroll
+      for (int q = 0; q < IPT / 2; ++q) o[q] = make_uint2(val[2 * q], val[2 * q + 1]);
     } else {
 #pragma unroll
       for (int q = 0; q < IPT; ++q)

@@ -118,9 +118,11 @@ def test_tuning_table_without_gpu(lib):
     assert ps.ps_tune_get(0, True) == (16, 2)
     assert ps.ps_tune_get(0, False) == (8, 2)
     with pytest.raises(ps.PowersortError):
-        ps.ps_tune_set(0, True, 10, 2)  # not a configuration the library carries
+        ps.ps_tune_set(0, True, 10, 3)  # not a configuration the library carries
     ps.ps_tune_set(0, True, 0, 0)
     assert ps.ps_tune_get(0, True) == (8, 2)
+    assert ps.ps_tune_get(2, True) == (6, 2)  # 8-byte keys: 6 items per thread by default
+    assert ps.ps_tune_get(2, False) == (6, 2)
 
 
 def test_binding_rejects_mismatched_buffers_without_gpu(lib):

@@ -9,7 +9,7 @@ import workloads
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = [(12, 2), (12, 3), (12, 4), (8, 2), (8, 3), (16, 2)]
+VARIANTS = [(12, 2), (12, 3), (12, 4), (8, 2), (8, 3), (16, 2), (6, 2), (10, 2)]
 
 
 @pytest.fixture(scope="module")
@@ -51,7 +51,7 @@ def test_autotune_picks_a_configuration(ps):
     dv = torch.from_numpy(vals.view(np.int32)).cuda()
     before_k, before_v = dk.clone(), dv.clone()
     res = ps.ps_autotune(dk, dv, key_type=0)
-    assert len(res["variants"]) == len(VARIANTS)
+    assert [(v["items_per_thread"], v["stages"]) for v in res["variants"]] == VARIANTS
     assert all(v["ms"] > 0 for v in res["variants"])
     best = min(res["variants"], key=lambda v: v["ms"])
     assert (res["items_per_thread"], res["stages"]) == (best["items_per_thread"], best["stages"])
@@ -87,3 +87,19 @@ def test_tuned_entries_by_kind_and_size_bucket(ps):
     np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
     ps.ps_tune_set(0, True, 0, 0)
     assert ps.ps_tune_get_for(0, True, keys.size, segmented=True) == (8, 2)
+
+
+def test_autotune_u64_times_every_configuration(ps):
+    """The autotuner times all eight configurations on 8-byte keys too, and the tuned sort equals
+    the oracle."""
+    keys, vals = workloads.pareto_u64(1 << 20, seed=5, distinct=1000)
+    dk = torch.from_numpy(keys.view(np.int64)).cuda()
+    dv = torch.from_numpy(vals.view(np.int32)).cuda()
+    res = ps.ps_autotune(dk, dv, key_type=2)
+    assert [(v["items_per_thread"], v["stages"]) for v in res["variants"]] == VARIANTS
+    assert ps.ps_tune_get_for(2, True, keys.size) == (res["items_per_thread"], res["stages"])
+    ps.ps_sort(dk, dv, key_type=2)
+    ref = oracle.powersort(keys, vals, kt="u64")
+    np.testing.assert_array_equal(dk.cpu().numpy().view(np.uint64), ref.keys)
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+    ps.ps_tune_set(2, True, 0, 0)
