@@ -300,17 +300,30 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
       sp[t * 9 + k] = cw;
     }
     __syncthreads();
-    // coalesced write-out
-    for (int i = t; i < kTreeTile; i += kTreeThreads) {
-      const int32_t u = u0 + i;
-      if (u > r) break;
-      const uint32_t cnt = (sp[(i >> 2) + (i >> 5)] >> (8 * (i & 3))) & 0xFFu;
-      if (cnt != 0xFFu) {
-        const int32_t j = virt_to_j<kBackward>(u, r);
-        if (!PS_IN_RANGE(j, r + 1)) continue;
-        near_out[j] = virt_to_j<kBackward>(s_near[i + (i >> 5)], r);
-        if (kBackward) depth_acc[j] = (uint8_t)(depth_acc[j] + cnt);
-        else depth_acc[j] = (uint8_t)cnt;
+    // coalesced write-out, kGroup indices per thread at a time: the backward pass adds its counts
+    // to the forward pass's, and loading the group's old counts before its stores keeps those
+    // loads off a load-store chain (byte stores may alias any load)
+    constexpr int kGroup = 8;
+#pragma unroll 1
+    for (int i0 = t; i0 < kTreeTile; i0 += kGroup * kTreeThreads) {
+      uint32_t cnt[kGroup], old[kGroup];
+      int32_t jj[kGroup];
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) {
+        const int i = i0 + q * kTreeThreads;
+        const int32_t u = u0 + i;
+        cnt[q] = (u <= r) ? (sp[(i >> 2) + (i >> 5)] >> (8 * (i & 3))) & 0xFFu : 0xFFu;
+        jj[q] = virt_to_j<kBackward>(u, r);
+        if (!PS_IN_RANGE(jj[q], r + 1)) cnt[q] = 0xFFu;
+        old[q] = (kBackward && cnt[q] != 0xFFu) ? depth_acc[jj[q]] : 0u;
+      }
+#pragma unroll
+      for (int q = 0; q < kGroup; ++q) {
+        const int i = i0 + q * kTreeThreads;
+        if (cnt[q] != 0xFFu) {
+          near_out[jj[q]] = virt_to_j<kBackward>(s_near[i + (i >> 5)], r);
+          depth_acc[jj[q]] = (uint8_t)(old[q] + cnt[q]);
+        }
       }
     }
     __syncthreads();
@@ -633,13 +646,26 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const int tgrid = persistent_blocks(4);
+  // the apply kernel's shared memory allows fewer resident CTAs per SM than the summary's; both
+  // grids are what is resident at once, so no CTA waits for a second wave
+  static int apply_per_sm = 0, summary_per_sm = 0;
+  if (apply_per_sm == 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&apply_per_sm, tree_apply_kernel<true>,
+                                                                  kTreeThreads, kTreeApplySmem);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&summary_per_sm, tree_summary_kernel<true>, kTreeThreads,
+                                                        kTreeSummarySmem);
+    if (e != cudaSuccess) return e;
+    apply_per_sm = std::max(1, std::min(apply_per_sm, 4));
+    summary_per_sm = std::max(1, std::min(summary_per_sm, 4));
+  }
+  const int tgrid = persistent_blocks(summary_per_sm), agrid = persistent_blocks(apply_per_sm);
   tree_summary_kernel<false><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
   tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
-  tree_apply_kernel<false><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeL, c.ndepth);
+  tree_apply_kernel<false><<<agrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeL, c.ndepth);
   tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
   tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
-  tree_apply_kernel<true><<<tgrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
+  tree_apply_kernel<true><<<agrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro,
                                           c.sub_lim, micro_tile(c.key_bytes), c.small_tasks, c.leaf_items, c.leaf_tile_off,
                                           c.level_items, c.level_tile_off, c.level_cap, (uint32_t)std::min<int64_t>(c.run_cap, 0xffffffffll), c.merge_tile,
