@@ -31,40 +31,69 @@ __device__ __forceinline__ uint64_t div_invariant(uint64_t a, uint64_t d, uint64
   return q;
 }
 
-__global__ void __launch_bounds__(256, 8) node_power_kernel(const pos_t* __restrict__ S, const int32_t* __restrict__ run_seg,
+// A thread computes the powers of four consecutive boundaries j0 .. j0+3 (one 32-bit word of P):
+// with q_k = floor((S[k] + S[k+1] - 2 base) 2^31 / (2 ns)) the scaled midpoint of run k in its
+// segment, boundary j has x = q_{j-1} and y = q_j, so five divisions serve the four powers.
+__global__ void __launch_bounds__(256, 6) node_power_kernel(const pos_t* __restrict__ S, const int32_t* __restrict__ run_seg,
                                   const int64_t* __restrict__ offsets, int64_t n, uint8_t* __restrict__ P,
                                   PlanHeader* __restrict__ hdr) {
   const int32_t r = hdr->runs;
+  const int32_t words = r / 4 + 1;  // P[0 .. r] as whole words (the allocation covers them)
   int32_t cached_seg = -1;
   int64_t base = 0, ns = n;
   uint64_t two_n = 2 * (uint64_t)n, m = ~0ull / (2 * (uint64_t)max(n, (int64_t)1));
   bool bad = false;
-  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= r; j += gridDim.x * blockDim.x) {
-    uint8_t p = 0;
-    if (j >= 1 && j < r) {
-      bool same = true;
-      if (run_seg != nullptr) {
-        const int32_t sg = run_seg[j];
-        same = (run_seg[j - 1] == sg);
-        if (same && sg != cached_seg) {
-          cached_seg = sg;
-          base = offsets[sg];
-          ns = offsets[sg + 1] - base;
-          two_n = 2 * (uint64_t)(ns > 0 ? ns : 1);
-          m = ~0ull / two_n;
+  for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < words; g += gridDim.x * blockDim.x) {
+    const int32_t j0 = 4 * g;
+    // S[j0 - 1 .. j0 + 4]: entries past r are never used
+    pos_t s[6];
+    s[0] = j0 >= 1 ? S[j0 - 1] : 0u;
+    if (j0 + 4 <= r) {
+      const uint4 w = *(const uint4*)(S + j0);  // S is 16-byte aligned and j0 a multiple of 4
+      s[1] = w.x;
+      s[2] = w.y;
+      s[3] = w.z;
+      s[4] = w.w;
+      s[5] = S[j0 + 4];
+    } else {
+#pragma unroll
+      for (int e = 1; e < 6; ++e) s[e] = (j0 - 1 + e <= r) ? S[j0 - 1 + e] : 0u;
+    }
+    uint32_t q[5];
+    int32_t sg[5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {  // run k = j0 - 1 + e, for 0 <= k < r
+      const int32_t k = j0 - 1 + e;
+      q[e] = 0;
+      sg[e] = -1;
+      if (k >= 0 && k < r) {
+        if (run_seg != nullptr) {
+          sg[e] = run_seg[k];
+          if (sg[e] != cached_seg) {
+            cached_seg = sg[e];
+            base = offsets[sg[e]];
+            ns = offsets[sg[e] + 1] - base;
+            two_n = 2 * (uint64_t)(ns > 0 ? ns : 1);
+            m = ~0ull / two_n;
+          }
+          if (ns <= 0) sg[e] = -2 - k;  // only with invalid offsets, which the host rejects
+        } else {
+          sg[e] = 0;
         }
-        if (ns <= 0) same = false;  // only with invalid offsets, which the host rejects
-      }
-      if (same) {
-        const uint64_t l2 = (uint64_t)((int64_t)S[j - 1] + S[j] - 2 * base);
-        const uint64_t r2 = (uint64_t)((int64_t)S[j] + S[j + 1] - 2 * base);
-        const uint32_t x = (uint32_t)div_invariant(l2 << 31, two_n, m);
-        const uint32_t y = (uint32_t)div_invariant(r2 << 31, two_n, m);
-        bad |= x == y;  // excluded by the run-length argument above
-        p = (uint8_t)__clz(x ^ y);
+        const uint64_t mid2 = (uint64_t)((int64_t)s[e] + s[e + 1] - 2 * base);
+        q[e] = (uint32_t)div_invariant(mid2 << 31, two_n, m);
       }
     }
-    P[j] = p;
+    uint32_t w = 0;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int32_t j = j0 + e;
+      if (j >= 1 && j < r && sg[e] >= 0 && sg[e] == sg[e + 1]) {
+        bad |= q[e] == q[e + 1];  // excluded by the run-length argument above
+        w |= (uint32_t)__clz(q[e] ^ q[e + 1]) << (8 * e);
+      }
+    }
+    ((uint32_t*)P)[g] = w;
   }
   if (bad) post_status(&hdr->status, nullptr, kDevInternal);
 }
@@ -314,7 +343,7 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
         const int32_t u = u0 + i;
         cnt[q] = (u <= r) ? (sp[(i >> 2) + (i >> 5)] >> (8 * (i & 3))) & 0xFFu : 0xFFu;
         jj[q] = virt_to_j<kBackward>(u, r);
-        if (!PS_IN_RANGE(jj[q], r + 1)) cnt[q] = 0xFFu;
+        if (cnt[q] != 0xFFu && !PS_IN_RANGE(jj[q], r + 1)) cnt[q] = 0xFFu;
         old[q] = (kBackward && cnt[q] != 0xFFu) ? depth_acc[jj[q]] : 0u;
       }
 #pragma unroll
@@ -593,8 +622,8 @@ __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int32_
 // ---------------------------------------------------------------------------------------
 // Host launchers for the key-independent stages.
 // ---------------------------------------------------------------------------------------
-// Grid of per_sm resident CTAs per SM (the kernels launched with 8 per SM are bounded to 32
-// registers, so all of them are resident at once).
+// Grid of per_sm resident CTAs per SM (each kernel's launch bounds allow the per_sm it is
+// launched with, so all of its CTAs are resident at once).
 static int persistent_blocks(int per_sm) {
   static int sms = 0;
   if (sms == 0) {
@@ -637,7 +666,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
                                             c.hdr);
     return cudaGetLastError();
   }
-  node_power_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
+  node_power_kernel<<<persistent_blocks(6), 256, 0, c.stream>>>(c.S, c.run_seg, c.offsets, c.n, c.P, c.hdr);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaSuccess;
