@@ -247,6 +247,12 @@ struct ThreadRuns {
   }
   // walk the chain from its first start; returns the number of starts and the exit state
   __device__ __forceinline__ void chain(int pos, uint32_t none_state, uint32_t& cnt, uint32_t& exit_state) const {
+    if ((F >> 1) == 0) {  // no forced start past position 0: all starts at once
+      const uint64_t m = chain_starts(pos);
+      cnt = (uint32_t)__popcll(m);
+      exit_state = m ? open_state(63 - __clzll((long long)m)) : none_state;
+      return;
+    }
     cnt = 0;
     exit_state = none_state;
     while (pos < nvalid) {
@@ -254,6 +260,23 @@ struct ThreadRuns {
       exit_state = open_state(pos);
       pos = next_start(pos);
     }
+  }
+  // The run starts of the chain that begins at pos0, as a mask, for a view with no forced start
+  // past position 0.  After a start s the next one is the first q >= s + 2 whose pair disagrees
+  // with the run's direction L[s+1], which is the first change point (q with L[q] != L[q-1]) at
+  // or after s + 2.  Inside a maximal block of consecutive change points the chain therefore takes
+  // every other point from the block's first one, and it always takes a block's first point (the
+  // position before it is no change point, so the previous start lies at least two below it).
+  // With pos0 made the first point of its block, the starts are the even-offset points of every
+  // block: the blocks that begin at even positions keep their even bits, the others their odd
+  // bits (a block's bits are found by adding its first bit, whose carry runs through the block).
+  __device__ __forceinline__ uint64_t chain_starts(int pos0) const {
+    if (pos0 >= nvalid) return 0ull;
+    const uint64_t c = ((L ^ (L << 1)) & (~0ull << (pos0 + 1))) | (1ull << pos0);
+    constexpr uint64_t kEven = 0x5555555555555555ull;
+    const uint64_t even_firsts = c & ~(c << 1) & kEven;
+    const uint64_t even_blocks = ((c + even_firsts) ^ c) & c;
+    return ((even_blocks & kEven) | (c & ~even_blocks & ~kEven)) & valid;
   }
   __device__ __forceinline__ Fn aggregate() const {
     if (nvalid == 0) return fn_identity();
@@ -354,7 +377,11 @@ detect_scan_kernel(const uint64_t* __restrict__ tile_agg, int32_t ntiles, int64_
 }
 
 // Pass 3: every thread replays its positions from its entry state and writes its run starts
-// S[k], directions run_desc[k] and segments run_seg[k] at their global ranks.
+// S[k], directions run_desc[k] and segments run_seg[k] at their global ranks.  Without segments a
+// tile's runs (at most kDetectTile / 2 of them: every greedy run but the array's last has two
+// elements or more) are collected in shared memory and written out coalesced.
+constexpr int kEmitStage = kDetectTile / 2 + 32;
+
 template <class K>
 __global__ void __launch_bounds__(kDetectThreads)
 detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offsets, int32_t count,
@@ -362,6 +389,9 @@ detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offse
                    const uint64_t* __restrict__ thr_F, const uint32_t* __restrict__ thr_fn,
                    pos_t* __restrict__ S, uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
   __shared__ Fn warp_tot[kDetectThreads / 32];
+  __shared__ pos_t s_start[kEmitStage];
+  __shared__ uint8_t s_desc[kEmitStage];
+  __shared__ uint32_t s_count;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
   ThreadRuns<K> tr;
@@ -380,30 +410,57 @@ detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offse
   Fn wp = fn_identity();
   for (int w = 0; w < warp; ++w) wp = fn_then(wp, warp_tot[w]);
   excl = fn_then(wp, excl);
-  if (tr.nvalid == 0) return;
+  const bool staged = offsets == nullptr;  // uniform over the grid
   const uint64_t pre = tile_pre[blockIdx.x];
   const uint32_t tile_entry = (uint32_t)(pre & 3u);
   const uint64_t tile_base = pre >> 2;
   const uint32_t entry = fn_exit(excl, tile_entry);  // state at position p0 - 1
   uint64_t idx = tile_base + fn_cnt(excl, tile_entry);
-  int pos;
-  if (tr.F & 1ull) pos = 0;
-  else if (entry == 0) pos = tr.first_start((uint32_t)(tr.L & 1ull));
-  else pos = tr.first_start(entry == 1 ? 1u : 0u);
-  int32_t seg = 0;
-  if (offsets != nullptr) seg = segment_of(offsets, count, tr.p0);
-  while (pos < tr.nvalid) {
+  auto emit = [&](int pos, int32_t seg) {
     const int64_t p = tr.p0 + pos;
-    if (offsets != nullptr && ((tr.F >> pos) & 1ull)) seg = segment_of(offsets, count, p);
     // descending iff the pair (p, p+1) lies inside the segment and is strictly decreasing
     const bool desc = (p + 1 < n) && !((tr.F >> (pos + 1)) & 1ull) && !((tr.L >> (pos + 1)) & 1ull);
-    if (idx < (uint64_t)run_cap) {  // always true when the tile counts are consistent
+    const uint64_t local = idx - tile_base;
+    if (staged && local < (uint64_t)kEmitStage) {
+      s_start[local] = (pos_t)p;
+      s_desc[local] = desc ? 1 : 0;
+    } else if (idx < (uint64_t)run_cap) {  // always true when the tile counts are consistent
       S[idx] = (pos_t)p;
       run_desc[idx] = desc ? 1 : 0;
       if (run_seg) run_seg[idx] = seg;
     }
     ++idx;
-    pos = tr.next_start(pos);
+  };
+  if (tr.nvalid > 0) {
+    int pos;
+    if (tr.F & 1ull) pos = 0;
+    else if (entry == 0) pos = tr.first_start((uint32_t)(tr.L & 1ull));
+    else pos = tr.first_start(entry == 1 ? 1u : 0u);
+    if ((tr.F >> 1) == 0) {  // no segment start past the thread's first position
+      const int32_t seg = (offsets != nullptr) ? segment_of(offsets, count, tr.p0) : 0;
+      uint64_t m = tr.chain_starts(pos);
+      while (m) {
+        emit(__ffsll((long long)m) - 1, seg);
+        m &= m - 1;
+      }
+    } else {
+      int32_t seg = segment_of(offsets, count, tr.p0);
+      while (pos < tr.nvalid) {
+        if ((tr.F >> pos) & 1ull) seg = segment_of(offsets, count, tr.p0 + pos);
+        emit(pos, seg);
+        pos = tr.next_start(pos);
+      }
+    }
+  }
+  if (!staged) return;
+  if (tid == kDetectThreads - 1) s_count = (uint32_t)min(idx - tile_base, (uint64_t)kEmitStage);
+  __syncthreads();
+  const uint32_t cnt = s_count;
+  for (uint32_t i = tid; i < cnt; i += kDetectThreads) {
+    if (tile_base + i < (uint64_t)run_cap) {
+      S[tile_base + i] = s_start[i];
+      run_desc[tile_base + i] = s_desc[i];
+    }
   }
 }
 
