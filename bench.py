@@ -750,13 +750,121 @@ def main():
     ap.add_argument("--once", choices=["runs", "perm", "runs_minrun24", "perm_minrun24", "u64"], default=None,
                     help="profiling driver: exactly one sort of the headline (runs), permutation or uint64 "
                          "Pareto(1.2) workload (*_minrun24: runs extended to 24) at --n, no warm-up, no JSON line")
+    ap.add_argument("--l2-sweep", action="store_true",
+                    help="measurement of the L2 against HBM: a streaming copy kernel over buffer pairs of "
+                         "4 MB .. 2 GB, and the level passes of sorts of 2^20 .. 2^24 headline-like keys; "
+                         "one JSON line, nothing else")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # at least 3 untimed warm-up steps
     if args.once:
         return run_once(args)
+    if args.l2_sweep:
+        return run_l2_sweep(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
+
+
+# Streaming copy for the L2 sweep: every thread copies its own fixed 16-byte words from one
+# buffer to the other and back, `iters` times, with L2-only (.cg) loads and stores and no
+# dependence between threads, so the rate is the memory system's, not a synchronisation's.
+_PINGPONG_CU = r"""
+#include <cstdint>
+#include <cuda_runtime.h>
+__device__ __forceinline__ uint4 ldcg(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.cg.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void stcg(uint4* p, uint4 v) {
+  asm volatile("st.global.cg.v4.u32 [%0], {%1,%2,%3,%4};" :: "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+}
+__global__ void pingpong(uint4* a, uint4* b, long long n16, int iters) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (int it = 0; it < iters; ++it) {
+    const uint4* src = (it & 1) ? b : a;
+    uint4* dst = (it & 1) ? a : b;
+    for (long long i = t0; i < n16; i += stride) {
+      uint4 v = ldcg(src + i);
+      v.x += 1u;
+      stcg(dst + i, v);
+    }
+  }
+}
+extern "C" int pingpong_launch(void* a, void* b, long long n16, int iters, int grid, void* stream) {
+  pingpong<<<grid, 256, 0, (cudaStream_t)stream>>>((uint4*)a, (uint4*)b, n16, iters);
+  return (int)cudaGetLastError();
+}
+"""
+
+
+def run_l2_sweep(args):
+    """L2 against HBM on this GPU: the streaming rate for buffer pairs that fit the 129 MB L2 or
+    not, and what the level passes reach on arrays whose two buffers fit it."""
+    import ctypes
+    import tempfile
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1805_04154_gb300 import _build
+    _build.build()
+    import paper_1805_04154_gb300 as ps
+    ps.load()
+    tmp = tempfile.mkdtemp()
+    src, so = os.path.join(tmp, "pingpong.cu"), os.path.join(tmp, "pingpong.so")
+    with open(src, "w") as f:
+        f.write(_PINGPONG_CU)
+    subprocess.check_call([_build._nvcc(), *_build.ARCH, "-O3", "-shared", "-Xcompiler", "-fPIC", src, "-o", so])
+    lib = ctypes.CDLL(so)
+    lib.pingpong_launch.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_longlong, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_void_p]
+    s = torch.cuda.current_stream()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    copy = []
+    for mb in (4, 8, 16, 32, 48, 64, 96, 128, 512, 2048):
+        nb = mb << 20
+        a = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+        b = torch.zeros_like(a)
+        iters = max(2, min(4000, int(0.02 * 6e12 / (2 * nb))))  # about 20 ms of copying
+        best = 0.0
+        for grid in (sms * 4, sms * 8):
+            assert lib.pingpong_launch(a.data_ptr(), b.data_ptr(), nb // 16, 2, grid, s.cuda_stream) == 0
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            assert lib.pingpong_launch(a.data_ptr(), b.data_ptr(), nb // 16, iters, grid, s.cuda_stream) == 0
+            e1.record(s)
+            torch.cuda.synchronize()
+            best = max(best, 2 * nb * iters / e0.elapsed_time(e1) / 1e6)
+        copy.append({"mb_per_buffer": mb, "gbs": round(best, 1)})
+        del a, b
+    sorts = []
+    for n in (1 << 20, 1 << 22, 1 << 24, N_DEFAULT):
+        keys, vals = workloads.runs_i32(n, SEED, max_len=2 * int(N_DEFAULT ** 0.5))
+        dk0 = torch.from_numpy(keys).cuda()
+        dv0 = torch.from_numpy(vals.view(np.int32)).cuda()
+        ws = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n), dtype=torch.uint8, device="cuda")
+        dk, dv = dk0.clone(), dv0.clone()
+        reps = 10
+        for i in range(reps + 3):
+            if i == 3:
+                torch.cuda.synchronize()
+                ps.ps_profile_enable(True)
+            dk.copy_(dk0)
+            dv.copy_(dv0)
+            ps.ps_sort_ws(dk, dv, ws, key_type=ps.PS_KEY_I32)
+        torch.cuda.synchronize()
+        prof = ps.ps_profile_read()["level_pass"]
+        ps.ps_profile_enable(False)
+        sorts.append({"n": n, "working_set_mb": round(2 * n * 8 / 2 ** 20, 1), "level_passes": prof["launches"] // reps,
+                      "level_ms": round(prof["ms"] / reps, 4), "gbs": round(prof["bytes"] / prof["ms"] / 1e6, 1)})
+        del dk0, dv0, dk, dv, ws
+        torch.cuda.empty_cache()
+    print(json.dumps({"l2_sweep": {"copy": copy, "level_pass": sorts, "peak_hbm_gbs": _peaks()[0],
+                                   "note": "copy: best of grids 4 and 8 CTAs per SM, read + write bytes; "
+                                           "level_pass: algorithmic bytes of all level passes / their CUDA-event time"}}))
+    return 0
 
 
 def run_once(args):
