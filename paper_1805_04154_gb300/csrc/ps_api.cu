@@ -498,11 +498,23 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   if (!c.lib_status) return PS_ERR_CUDA;
   apply_pass_config(c, kt, vals != nullptr, n, segmented);
   const KeyLaunch* kl = launch_for(kt);
-  // deepest node: depth < power <= floor(lg n) + 1 for Alg. 2; the plan's limit for Alg. 1
+  // Deepest node a level pass can meet: depth < power (powers grow from a node to its children)
+  // and power <= floor(lg n) + 1 for Alg. 2; the plan's limit for Alg. 1.  Only nodes larger than
+  // sub_lim reach a level pass, and a node of power p spans fewer than 4 n_s / 2^p elements of its
+  // segment (n_s <= n).  The boundaries inside its range all have power >= p, so the midpoints
+  // c_L < .. < c_R' of its runs (normalised by n_s) lie in one dyadic interval of length 2^(1-p).
+  // Its first run starts after 2 c_L - c_(L+1) and its last ends before 2 c_R' - c_(R'-1) (a run's
+  // half length is below the distance to its neighbour's midpoint), so its size / n_s is below
+  // 2 (c_R' - c_L) - (c_(R'-1) - c_(L+1)) <= 2 (c_R' - c_L) with three runs or more, and equals
+  // 2 (c_R' - c_L) with two; both are below 2 * 2^(1-p).  So 2^p < 4 n / sub_lim, and launches for
+  // deeper levels would find no node.
   int maxd = kMaxLevels - 1;
   if (tree == PS_TREE_POWERSORT) {
     maxd = 0;
     while (maxd < kMaxLevels - 1 && ((int64_t)1 << (maxd + 1)) <= n) ++maxd;
+    int pmax = 0;  // smallest p with 2^p >= 4 n / sub_lim: every level-pass node has power < pmax
+    while (pmax < 62 && ((int64_t)c.sub_lim << pmax) < 4 * n) ++pmax;
+    maxd = std::min(maxd, std::max(pmax - 2, 0));
   }
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
   {
