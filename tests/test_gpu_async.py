@@ -168,3 +168,38 @@ def test_device_driven_tasks_beyond_the_one_task_grid():
                        capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "overflow path ok" in r.stdout
+
+
+def _comb(lengths, seed):
+    """int32 keys made of ascending runs of the given lengths (random values), uint32 index payload."""
+    rng = np.random.default_rng(seed)
+    parts = [np.sort(rng.integers(-(1 << 31), 1 << 31, size=int(m), dtype=np.int64)).astype(np.int32) for m in lengths]
+    keys = np.concatenate(parts)
+    return keys, np.arange(keys.size, dtype=np.uint32)
+
+
+@pytest.mark.parametrize("order", ["halving", "doubling", "nested"])
+def test_async_deep_trees_of_large_nodes(ps, order):
+    """Merge trees whose nodes larger than the subtree limit reach the greatest depth the
+    device-driven entry launches level passes for (a node of power p spans fewer than 4n/2^p
+    elements): halving and doubling run lengths, and a large run between two such combs.  A bound
+    that stopped too shallow would leave the deepest merges undone."""
+    halving = [1 << k for k in range(21, 11, -1)] + [4096] * 8
+    if order == "halving":
+        lengths = halving
+    elif order == "doubling":
+        lengths = halving[::-1]
+    else:
+        lengths = halving[::-1] + [1 << 22] + halving
+    keys, vals = _comb(lengths, seed=len(lengths))
+    n = keys.size
+    ref = oracle.powersort(keys, vals)
+    _, depth, power = oracle.powersort_cost(np.array(lengths, np.int64))
+    dk, dv = _dev(keys), _dev(vals)
+    ps.ps_sort_async_ws(dk, dv, _ws(ps, 0, n), key_type=0)
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref.keys)
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref.vals)
+    # the input does reach deep: a leaf larger than the subtree limit at depth >= 8
+    big = np.array(lengths) > 4096
+    assert depth[big].max() >= 8
