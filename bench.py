@@ -248,11 +248,12 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
     # the same batch as one captured CUDA graph of the device-driven entry, replayed
     gk, gv = k0.clone(), v0.clone()
     wsg = torch.empty(ps.ps_workspace_size(ps.PS_KEY_I32, True, n, True), dtype=torch.uint8, device=dev)
-    ps.ps_sort_async_ws(gk, gv, wsg, offsets=doff, key_type=ps.PS_KEY_I32, stream=stream)
+    longest = int(np.diff(off).max())  # the batch's longest array, known to the caller
+    ps.ps_sort_async_bounded_ws(gk, gv, wsg, longest, offsets=doff, key_type=ps.PS_KEY_I32, stream=stream)
     torch.cuda.synchronize(dev)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        ps.ps_sort_async_ws(gk, gv, wsg, offsets=doff, key_type=ps.PS_KEY_I32)
+        ps.ps_sort_async_bounded_ws(gk, gv, wsg, longest, offsets=doff, key_type=ps.PS_KEY_I32)
     gbest = None
     for rep in range(reps + 1):
         gk.copy_(k0)
@@ -297,7 +298,8 @@ def measure_batched(ps, dev, count: int, reps: int = 3):
             "level_pass_config": {"autotune": tune,
                                   "in_use": list(ps.ps_tune_get_for(ps.PS_KEY_I32, True, n, True))},
             "batched_entry": "ps_sort_segmented_ws (one call)",
-            "graph_entry": "ps_sort_async_ws captured once in a CUDA graph, replayed",
+            "graph_entry": "ps_sort_async_bounded_ws (device-driven, the batch's longest array as the bound) "
+                           "captured once in a CUDA graph, replayed",
             "plain_entry": "ps_sort_ws per array"}
 
 

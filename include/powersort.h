@@ -229,6 +229,19 @@ ps_status ps_tune_get_for(int key_type, int has_vals, int64_t n, int segmented, 
 ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
                            int64_t count, int tree, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ps_sort_async_ws with powersort's tree (Alg. 2) for callers that know the longest segment:
+ * every segment (the whole array when d_offsets is NULL) holds at most max_segment elements.
+ * The level passes are launched only down to the deepest node a segment of that length can give
+ * a level pass (a node of power p spans fewer than 4 n_s / 2^p of its segment's n_s elements, and
+ * depth < power; Definition "Node Power"), so a batch of short segments queues fewer launches.
+ * The bound is checked on the device with the offsets: a longer segment is reported by
+ * ps_stream_status as rejected offsets and nothing is moved.  PS_ERR_INVALID_ARG for
+ * max_segment < 1, or without offsets for n > max_segment.  Workspace and capture rules as for
+ * ps_sort_async_ws (tree PS_TREE_POWERSORT). */
+ps_status ps_sort_async_bounded_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                                   int64_t count, int64_t max_segment, void* workspace, size_t workspace_bytes,
+                                   void* stream);
+
 /* ps_analyze with the merge tree chosen by `tree`.  For PS_TREE_PEEKSORT, power[j] receives the
  * node's depth + 1 at every internal boundary (0 at sentinels and segment borders): the order in
  * which the plan finds parents (a leaf's parent is the larger of its two boundaries, a node's

@@ -23,7 +23,7 @@ __all__ = [
     "ps_merge_cost", "ps_analyze", "ps_sort_stats", "ps_stream_status", "ps_status_string",
     "ps_version", "key_type_of", "ps_sort_host", "ps_profile_enable", "ps_profile_read",
     "ps_launch_count", "STAGES", "PS_TREE_POWERSORT", "PS_TREE_PEEKSORT", "ps_sort_tree_ws",
-    "ps_sort_tree", "ps_sort_host_ws", "ps_sort_async_ws", "ps_autotune", "ps_tune_set", "ps_tune_get",
+    "ps_sort_tree", "ps_sort_host_ws", "ps_sort_async_ws", "ps_sort_async_bounded_ws", "ps_autotune", "ps_tune_set", "ps_tune_get",
 ]
 
 STAGES = ["detect", "meta", "subtree_smem", "leaf_place", "unused", "level_pass"]
@@ -90,6 +90,7 @@ def load():
                 "ps_workspace_size_tree": ([i32, i32, i64, i32, i32], sz),
                 "ps_sort_host_ws": ([i32, vp, vp, vp, vp, i64, vp, vp, vp, sz, vp], i32),
                 "ps_sort_async_ws": ([i32, vp, vp, i64, vp, i64, i32, vp, sz, vp], i32),
+                "ps_sort_async_bounded_ws": ([i32, vp, vp, i64, vp, i64, i64, vp, sz, vp], i32),
                 "ps_autotune": ([i32, vp, vp, i64, vp, vp], i32),
                 "ps_tune_set": ([i32, i32, i32, i32], i32),
                 "ps_tune_get": ([i32, i32, vp, vp], i32),
@@ -460,6 +461,21 @@ def ps_sort_async_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: t
     _check(load().ps_sort_async_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
                                    _dev_ptr(offsets, "offsets"), count, int(tree), _dev_ptr(workspace, "workspace"),
                                    _ws_bytes(workspace, keys), _stream_ptr(stream, keys.device)), "ps_sort_async_ws")
+
+
+def ps_sort_async_bounded_ws(keys: torch.Tensor, vals: torch.Tensor | None, workspace: torch.Tensor,
+                             max_segment: int, offsets: torch.Tensor | None = None, key_type: int | None = None,
+                             stream=None) -> None:
+    """ps_sort_async_ws (powersort's tree) for a caller that knows every segment holds at most
+    ``max_segment`` elements (checked on the device): fewer level-pass launches are queued."""
+    kt = _key_type(keys, key_type)
+    n = keys.numel()
+    _check_vals(vals, keys)
+    count = _segments(offsets, keys)
+    _check(load().ps_sort_async_bounded_ws(kt, _dev_ptr(keys, "keys"), _dev_ptr(vals, "vals"), n,
+                                           _dev_ptr(offsets, "offsets"), count, int(max_segment),
+                                           _dev_ptr(workspace, "workspace"), _ws_bytes(workspace, keys),
+                                           _stream_ptr(stream, keys.device)), "ps_sort_async_bounded_ws")
 
 
 class _Tune(ctypes.Structure):

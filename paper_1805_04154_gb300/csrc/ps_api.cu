@@ -474,10 +474,11 @@ ps_status run(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_of
 // work and can be captured into a CUDA graph.  Binary passes; errors found on the device reach
 // ps_stream_status, and with rejected segment offsets nothing is moved.
 ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets, int64_t count,
-                    bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, int tree) {
+                    bool segmented, void* ws, size_t ws_bytes, cudaStream_t s, int tree, int64_t max_segment = 0) {
   ps_status st = check_args(kt, keys, vals, n);
   if (st != PS_OK) return st;
   if (tree != PS_TREE_POWERSORT && tree != PS_TREE_PEEKSORT) return PS_ERR_INVALID_ARG;
+  if (max_segment < 0 || (!segmented && max_segment > 0 && n > max_segment)) return PS_ERR_INVALID_ARG;
   if (segmented && (!d_offsets || count < 1 || count >= ((int64_t)1 << 31))) return PS_ERR_INVALID_ARG;
   if (n <= 1) return PS_OK;
   Ctx c;
@@ -492,6 +493,7 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   c.n = n;
   c.offsets = segmented ? d_offsets : nullptr;
   c.count = segmented ? (int32_t)count : 1;
+  c.max_segment = max_segment;
   c.k[0] = keys;
   c.v[0] = vals;
   c.lib_status = lib_status_word(dev);
@@ -506,14 +508,16 @@ ps_status run_async(int kt, void* keys, uint32_t* vals, int64_t n, const int64_t
   // Its first run starts after 2 c_L - c_(L+1) and its last ends before 2 c_R' - c_(R'-1) (a run's
   // half length is below the distance to its neighbour's midpoint), so its size / n_s is below
   // 2 (c_R' - c_L) - (c_(R'-1) - c_(L+1)) <= 2 (c_R' - c_L) with three runs or more, and equals
-  // 2 (c_R' - c_L) with two; both are below 2 * 2^(1-p).  So 2^p < 4 n / sub_lim, and launches for
-  // deeper levels would find no node.
+  // 2 (c_R' - c_L) with two; both are below 2 * 2^(1-p).  So 2^p < 4 n_s / sub_lim for the
+  // longest segment n_s (n, or the caller's checked bound), and launches for deeper levels would
+  // find no node.
   int maxd = kMaxLevels - 1;
   if (tree == PS_TREE_POWERSORT) {
     maxd = 0;
     while (maxd < kMaxLevels - 1 && ((int64_t)1 << (maxd + 1)) <= n) ++maxd;
-    int pmax = 0;  // smallest p with 2^p >= 4 n / sub_lim: every level-pass node has power < pmax
-    while (pmax < 62 && ((int64_t)c.sub_lim << pmax) < 4 * n) ++pmax;
+    const int64_t ns = max_segment > 0 ? std::min(max_segment, n) : n;  // longest segment
+    int pmax = 0;  // smallest p with 2^p >= 4 ns / sub_lim: every level-pass node has power < pmax
+    while (pmax < 62 && ((int64_t)c.sub_lim << pmax) < 4 * ns) ++pmax;
     maxd = std::min(maxd, std::max(pmax - 2, 0));
   }
   PS_TRY(cudaMemsetAsync(c.hdr, 0, sizeof(PlanHeader), s));
@@ -837,6 +841,15 @@ ps_status ps_sort_async_ws(int key_type, void* keys, uint32_t* vals, int64_t n, 
   const bool seg = d_offsets != nullptr;
   return run_async(key_type, keys, vals, n, d_offsets, seg ? count : 1, seg, workspace, workspace_bytes,
                    (cudaStream_t)stream, tree);
+}
+
+ps_status ps_sort_async_bounded_ws(int key_type, void* keys, uint32_t* vals, int64_t n, const int64_t* d_offsets,
+                                   int64_t count, int64_t max_segment, void* workspace, size_t workspace_bytes,
+                                   void* stream) {
+  if (max_segment < 1) return PS_ERR_INVALID_ARG;
+  const bool seg = d_offsets != nullptr;
+  return run_async(key_type, keys, vals, n, d_offsets, seg ? count : 1, seg, workspace, workspace_bytes,
+                   (cudaStream_t)stream, PS_TREE_POWERSORT, max_segment);
 }
 
 size_t ps_workspace_size_tree(int key_type, int has_vals, int64_t n, int segmented, int tree) {

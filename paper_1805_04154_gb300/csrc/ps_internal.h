@@ -23,6 +23,7 @@ struct Ctx {
   bool has_vals = false;
   int64_t n = 0;         // elements (all segments), < kMaxElems
   const int64_t* offsets = nullptr;  // device, count+1 entries, or null for one array
+  int64_t max_segment = 0;  // > 0: the caller's bound on every segment's length (checked on the device)
   int32_t count = 1;
 
   void* k[2] = {nullptr, nullptr};   // [0] caller's keys, [1] scratch keys

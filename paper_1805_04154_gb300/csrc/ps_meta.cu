@@ -607,13 +607,14 @@ __global__ void header_out_kernel(const PlanHeader* __restrict__ hdr, PlanHeader
   __threadfence_system();
 }
 
-// Segment offsets must start at 0, be non-decreasing and end at n.
+// Segment offsets must start at 0, be non-decreasing and end at n (and, with a caller's bound,
+// no segment may be longer than max_segment).
 __global__ void check_offsets_kernel(const int64_t* __restrict__ offsets, int32_t count, int64_t n,
-                                     PlanHeader* __restrict__ hdr) {
+                                     int64_t max_segment, PlanHeader* __restrict__ hdr) {
   for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k <= count; k += gridDim.x * blockDim.x) {
     bool bad = false;
     if (k == 0) bad = offsets[0] != 0;
-    else bad = offsets[k] < offsets[k - 1];
+    else bad = offsets[k] < offsets[k - 1] || (max_segment > 0 && offsets[k] - offsets[k - 1] > max_segment);
     if (k == count) bad = bad || offsets[k] != n;
     if (bad) post_status(&hdr->status, nullptr, kDevBadOffsets);
   }
@@ -748,7 +749,7 @@ cudaError_t launch_wait_timeout_probe(uint32_t polls, uint32_t* lib_status, cuda
 }
 
 cudaError_t launch_check_offsets(const Ctx& c) {
-  check_offsets_kernel<<<persistent_blocks(1), 256, 0, c.stream>>>(c.offsets, c.count, c.n, c.hdr);
+  check_offsets_kernel<<<persistent_blocks(1), 256, 0, c.stream>>>(c.offsets, c.count, c.n, c.max_segment, c.hdr);
   return cudaGetLastError();
 }
 

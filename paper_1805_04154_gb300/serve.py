@@ -2,7 +2,7 @@
 
 Requests (host tensors of keys, optional 32-bit payload) are packed back to back into one of a
 few fixed device arena slots and sorted by a single device-driven segmented call
-(``ps_sort_async_ws``, no host round trip) per slot (each request is one segment, so each result
+(``ps_sort_async_bounded_ws``, no host round trip) per slot (each request is one segment, so each result
 is exactly what ``ps_sort`` gives for that request alone).  The slots rotate through three CUDA streams, so the host-to-device copies of one batch,
 the sort of another and the device-to-host copies of a third overlap on the GPU; a request that
 arrives while earlier batches are on the GPU joins the next batch as soon as a slot frees up.
@@ -198,13 +198,15 @@ class SortServer:
             h2d_done.record(self.h2d)
         self.compute.wait_event(h2d_done)
         # device-driven segmented sort: queued without a host round trip, so this thread goes on
-        # to the next batch while the GPU copies and sorts this one
-        st = load().ps_sort_async_ws(self.kt, ctypes.c_void_p(slot.dk.data_ptr()),
-                                     None if slot.dv is None else ctypes.c_void_p(slot.dv.data_ptr()), n,
-                                     ctypes.c_void_p(slot.doff.data_ptr()), count, 0,
-                                     ctypes.c_void_p(slot.ws.data_ptr()), slot.ws.numel(),
-                                     ctypes.c_void_p(self.compute.cuda_stream))
-        _check(st, "ps_sort_async_ws")
+        # to the next batch while the GPU copies and sorts this one; the batch's longest request
+        # bounds the level passes it needs
+        longest = max(r.keys.numel() for r in reqs)
+        st = load().ps_sort_async_bounded_ws(self.kt, ctypes.c_void_p(slot.dk.data_ptr()),
+                                             None if slot.dv is None else ctypes.c_void_p(slot.dv.data_ptr()), n,
+                                             ctypes.c_void_p(slot.doff.data_ptr()), count, max(longest, 1),
+                                             ctypes.c_void_p(slot.ws.data_ptr()), slot.ws.numel(),
+                                             ctypes.c_void_p(self.compute.cuda_stream))
+        _check(st, "ps_sort_async_bounded_ws")
         sort_done = torch.cuda.Event()
         sort_done.record(self.compute)
         self.d2h.wait_event(sort_done)

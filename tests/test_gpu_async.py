@@ -203,3 +203,56 @@ def test_async_deep_trees_of_large_nodes(ps, order):
     # the input does reach deep: a leaf larger than the subtree limit at depth >= 8
     big = np.array(lengths) > 4096
     assert depth[big].max() >= 8
+
+
+def test_bounded_entry_matches_oracle_and_checks_its_bound(ps):
+    """ps_sort_async_bounded_ws: the caller's bound on the longest segment trims the level-pass
+    launches and gives the oracle's result; a segment longer than the bound is rejected on the
+    device (nothing moves); a single array longer than the bound is an argument error; a CUDA
+    graph of the bounded call replays to the oracle's result."""
+    keys, vals, off = workloads.segmented_i32(400, seed=21, lo_exp=6, hi_exp=17)
+    longest = int(np.diff(off).max())
+    ref = oracle.sort_segmented(keys, vals, off)
+    n = keys.size
+    ws = _ws(ps, 0, n, True)
+    dk, dv, doff = _dev(keys), _dev(vals), torch.from_numpy(off).cuda()
+    before = ps.ps_launch_count()
+    ps.ps_sort_async_bounded_ws(dk, dv, ws, longest, offsets=doff, key_type=0)
+    bounded_launches = ps.ps_launch_count() - before
+    assert ps.ps_stream_status() == 0
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref[0])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref[1])
+    dk, dv = _dev(keys), _dev(vals)
+    before = ps.ps_launch_count()
+    ps.ps_sort_async_ws(dk, dv, ws, offsets=doff, key_type=0)
+    assert ps.ps_launch_count() - before > bounded_launches  # fewer level passes queued
+    assert ps.ps_stream_status() == 0
+    # a bound one element short of the longest segment: rejected on the device, nothing moves
+    dk, dv = _dev(keys), _dev(vals)
+    orig = dk.clone()
+    ps.ps_sort_async_bounded_ws(dk, dv, ws, longest - 1, offsets=doff, key_type=0)
+    assert ps.ps_stream_status() == 1
+    assert torch.equal(dk, orig)
+    assert ps.ps_stream_status() == 0
+    # one array: the bound is checked on the host
+    k1, v1 = workloads.runs_i32(5000, seed=22, max_len=200)
+    with pytest.raises(ps.PowersortError):
+        ps.ps_sort_async_bounded_ws(_dev(k1), _dev(v1), _ws(ps, 0, 5000), 4999, key_type=0)
+    # captured and replayed on new keys in the same segment layout
+    dk, dv = _dev(keys), _dev(vals)
+    ps.ps_sort_async_bounded_ws(dk, dv, ws, longest, offsets=doff, key_type=0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ps.ps_sort_async_bounded_ws(dk, dv, ws, longest, offsets=doff, key_type=0)
+    rng = np.random.default_rng(23)
+    k2 = rng.integers(-5000, 5000, size=n, dtype=np.int32)
+    v2 = np.arange(n, dtype=np.uint32)
+    dk.copy_(_dev(k2))
+    dv.copy_(_dev(v2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert ps.ps_stream_status() == 0
+    ref2 = oracle.sort_segmented(k2, v2, off)
+    np.testing.assert_array_equal(dk.cpu().numpy(), ref2[0])
+    np.testing.assert_array_equal(dv.cpu().numpy().view(np.uint32), ref2[1])
