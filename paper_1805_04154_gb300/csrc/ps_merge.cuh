@@ -531,7 +531,10 @@ subtree_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict_
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
                const uint8_t* __restrict__ micro, const int32_t* __restrict__ tasks, uint32_t cap,
                PlanHeader* __restrict__ hdr, uint32_t* lib_status) {
-  if (cap != 0 && ((hdr->status & kDevBadOffsets) || blockIdx.x >= min(hdr->n_small, cap))) return;
+  if (cap != 0) {  // both header words read at once: a surplus CTA returns after one load latency
+    const uint32_t n_small = hdr->n_small, status = hdr->status;
+    if (blockIdx.x >= min(n_small, cap) || (status & kDevBadOffsets)) return;
+  }
   subtree_task<K, V>(buf, S, run_desc, nodeL, nodeR, ndepth, ldepth, micro, tasks[blockIdx.x], hdr, lib_status);
 }
 
