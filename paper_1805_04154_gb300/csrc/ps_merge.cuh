@@ -522,10 +522,16 @@ __device__ __forceinline__ void subtree_task(Bufs buf, const pos_t* __restrict__
   }
 }
 
+// CTAs per SM the one-task kernel's register budget is sized for: 4 for 4-byte keys (shared
+// memory holds no more); 5 for 8-byte keys, whose tasks need 37 KB (measured 2.3% faster on the
+// uint64 Pareto sort than 4, and than 6, where the 40-register budget spills).
+template <class K>
+__host__ __device__ constexpr int sub_min_blocks() { return sizeof(typename K::T) == 8 ? 5 : 4; }
+
 // One CTA per task.  cap != 0: the grid covers the tasks up to a bound that the host computed
 // without the plan (device-driven calls); CTAs past the plan's count return at once.
 template <class K, bool V>
-__global__ void __launch_bounds__(kSubThreads, 4)
+__global__ void __launch_bounds__(kSubThreads, sub_min_blocks<K>())
 subtree_kernel(Bufs buf, const pos_t* __restrict__ S, const uint8_t* __restrict__ run_desc,
                const int32_t* __restrict__ nodeL, const int32_t* __restrict__ nodeR,
                const uint8_t* __restrict__ ndepth, const uint8_t* __restrict__ ldepth,
