@@ -160,12 +160,15 @@ __device__ __forceinline__ void stage_tile_powers(const uint8_t* __restrict__ P,
   }
 }
 
-// Thread chunk pass: s_last[v][t] = last virtual index of power v in the thread's chunk (or -1).
-__device__ __forceinline__ void chunk_last(const uint32_t* __restrict__ sp, int32_t u0,
-                                           int32_t (*s_last)[kTreeThreads]) {
+// Thread chunk pass: s_last[v][t] = last virtual index of power v in the thread's chunk, minus
+// base (or -1).  The summary stores virtual indices (base 0, 32-bit); the apply pass stores them
+// relative to its tile (base u0, 16-bit: a tile holds kTreeTile = 8192 indices).
+template <class L>
+__device__ __forceinline__ void chunk_last(const uint32_t* __restrict__ sp, int32_t u0, int32_t base,
+                                           L (*s_last)[kTreeThreads]) {
   const int t = threadIdx.x;
 #pragma unroll
-  for (int v = 0; v < 32; ++v) s_last[v][t] = -1;
+  for (int v = 0; v < 32; ++v) s_last[v][t] = (L)-1;
   const int32_t ub = u0 + t * kTreeChunk;
 #pragma unroll
   for (int k = 0; k < kTreeChunk / 4; ++k) {
@@ -173,7 +176,7 @@ __device__ __forceinline__ void chunk_last(const uint32_t* __restrict__ sp, int3
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const uint32_t p = (w >> (8 * e)) & 0xFFu;
-      if (p != kNoPower) s_last[p & 31][t] = ub + 4 * k + e;
+      if (p != kNoPower) s_last[p & 31][t] = (L)(ub + 4 * k + e - base);
     }
   }
 }
@@ -192,7 +195,7 @@ tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict_
     const int32_t u0 = tile * kTreeTile;
     stage_tile_powers<kBackward>(P, r, u0, sp);
     __syncthreads();
-    chunk_last(sp, u0, s_last);
+    chunk_last(sp, u0, 0, s_last);
     __syncthreads();
     // warp w reduces power values 4w..4w+3 over the tile's threads
 #pragma unroll
@@ -245,16 +248,27 @@ tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__
 }
 
 constexpr size_t kTreeSummarySmem = 32 * kTreeThreads * 4 + (kTreeTile / 4 + kTreeTile / 32) * 4;
-constexpr size_t kTreeApplySmem = kTreeSummarySmem + (size_t)(kTreeTile + kTreeTile / 32) * 4;
+// apply: 16-bit last-index table and nearest-smaller list (tile-relative), the staged powers, and
+// the tile prefix of every power: 42 KB, 5 CTAs per SM
+constexpr size_t kApplyLastBytes = 32 * kTreeThreads * 2;
+constexpr size_t kApplyStageBytes = (kTreeTile / 4 + kTreeTile / 32) * 4;
+constexpr size_t kApplyNearBytes = (size_t)(kTreeTile + kTreeTile / 32) * 2;
+constexpr size_t kTreeApplySmem = kApplyLastBytes + kApplyStageBytes + kApplyNearBytes + 32 * 4;
+static_assert(kTreeTile <= 32768, "tile-relative indices fit 16 bits");
 
 template <bool kBackward>
-__global__ void __launch_bounds__(kTreeThreads)
+__global__ void __launch_bounds__(kTreeThreads, 5)
 tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, const int32_t* __restrict__ prefix,
                   int32_t stride, int32_t* __restrict__ near_out, uint8_t* __restrict__ depth_acc) {
+  // Indices are kept relative to the tile start u0 in 16 bits: a last-index entry x >= 0 is the
+  // virtual index u0 + x; -1 stands for the tile prefix of its power, s_carry[v] (itself -1 when
+  // no index of that power precedes the tile).  A nearest-smaller entry that is a tile prefix is
+  // stored as -(v + 2), v its power.
   extern __shared__ __align__(16) uint8_t tsm[];
-  int32_t(*s_last)[kTreeThreads] = (int32_t(*)[kTreeThreads])tsm;
-  uint32_t* sp = (uint32_t*)(tsm + 32 * kTreeThreads * 4);
-  int32_t* s_near = (int32_t*)(tsm + kTreeSummarySmem);  // index i stored at i + i/32
+  int16_t(*s_last)[kTreeThreads] = (int16_t(*)[kTreeThreads])tsm;
+  uint32_t* sp = (uint32_t*)(tsm + kApplyLastBytes);
+  int16_t* s_near = (int16_t*)(tsm + kApplyLastBytes + kApplyStageBytes);  // index i stored at i + i/32
+  int32_t* s_carry = (int32_t*)(tsm + kApplyLastBytes + kApplyStageBytes + kApplyNearBytes);
   const int32_t r = hdr->runs;
   const int32_t ntiles = r / kTreeTile + 1;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -262,14 +276,16 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
   for (int32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int32_t u0 = tile * kTreeTile;
     stage_tile_powers<kBackward>(P, r, u0, sp);
+    if (t < 32) s_carry[t] = prefix[t * stride + tile];
     __syncthreads();
-    chunk_last(sp, u0, s_last);
+    chunk_last(sp, u0, u0, s_last);
     __syncthreads();
-    // exclusive max-scan of the chunk vectors over the tile's threads, after the tile prefix
+    // exclusive max-scan of the chunk vectors over the tile's threads (tile-relative; what no
+    // thread before supplies is the tile prefix, -1)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int v = warp * 4 + q;
-      int32_t carry = prefix[v * stride + tile];
+      int32_t carry = -1;
 #pragma unroll
       for (int x = 0; x < kTreeThreads / 32; ++x) {
         int32_t inc = s_last[v][x * 32 + lane];
@@ -280,18 +296,19 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
         }
         int32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
         if (lane == 0) exc = -1;
-        s_last[v][x * 32 + lane] = max(carry, exc);
+        s_last[v][x * 32 + lane] = (int16_t)max(carry, exc);
         carry = max(carry, __shfl_sync(0xffffffffu, inc, 31));
       }
     }
     __syncthreads();
-    // the stack in front of this thread's chunk
+    // the stack in front of this thread's chunk (virtual indices)
     uint32_t occ = 0;
     {
       int32_t M = -1;
 #pragma unroll
       for (int v = 0; v < 32; ++v) {
-        const int32_t x = s_last[v][t];
+        const int32_t x0 = s_last[v][t];
+        const int32_t x = x0 >= 0 ? u0 + x0 : s_carry[v];
         if (x > M) {
           occ |= 1u << v;
           M = x;
@@ -300,7 +317,7 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
     }
     // walk the chunk: nearest smaller on this side and the number of stack entries of power >= 1;
     // the count byte replaces the staged power (0xFF: no node here)
-    const int32_t ub = u0 + t * kTreeChunk;
+    const int32_t ub = t * kTreeChunk;  // tile-relative
 #pragma unroll
     for (int k = 0; k < kTreeChunk / 4; ++k) {
       const uint32_t w = sp[t * 9 + k];
@@ -309,20 +326,21 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
       for (int e = 0; e < 4; ++e) {
         const uint32_t p = (w >> (8 * e)) & 0xFFu;
         const int32_t u = ub + 4 * k + e;
-        const int i = t * kTreeChunk + 4 * k + e;
+        const int i = u;
         uint32_t cnt = 0xFFu;
         if (p == 0) {
           occ = 1u;
-          s_last[0][t] = u;
+          s_last[0][t] = (int16_t)u;
         } else if (p != kNoPower) {
           const uint32_t pp = p & 31u;
           const uint32_t om = occ & ((1u << pp) - 1u);
           if (om == 0u) bad = true;  // the power-0 sentinel is always below
           const int top = om ? 31 - __clz(om) : 0;
-          s_near[i + (i >> 5)] = s_last[top][t];
+          const int16_t x = s_last[top][t];
+          s_near[i + (i >> 5)] = x >= 0 ? x : (int16_t)(-(top + 2));
           cnt = (uint32_t)__popc(om) - 1u;
           occ = om | (1u << pp);
-          s_last[pp][t] = u;
+          s_last[pp][t] = (int16_t)u;
         }
         cw |= cnt << (8 * e);
       }
@@ -350,7 +368,9 @@ tree_apply_kernel(const uint8_t* __restrict__ P, PlanHeader* __restrict__ hdr, c
       for (int q = 0; q < kGroup; ++q) {
         const int i = i0 + q * kTreeThreads;
         if (cnt[q] != 0xFFu) {
-          near_out[jj[q]] = virt_to_j<kBackward>(s_near[i + (i >> 5)], r);
+          const int32_t x = s_near[i + (i >> 5)];
+          const int32_t nv = x >= 0 ? u0 + x : s_carry[-x - 2];
+          near_out[jj[q]] = virt_to_j<kBackward>(nv, r);
           depth_acc[jj[q]] = (uint8_t)(old[q] + cnt[q]);
         }
       }
@@ -676,8 +696,8 @@ cudaError_t launch_meta_stages(const Ctx& c) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  // the apply kernel's shared memory allows fewer resident CTAs per SM than the summary's; both
-  // grids are what is resident at once, so no CTA waits for a second wave
+  // both grids are what is resident at once (the apply kernel's 42 KB of shared memory and 48
+  // registers allow 5 CTAs per SM), so no CTA waits for a second wave
   static int apply_per_sm = 0, summary_per_sm = 0;
   if (apply_per_sm == 0) {
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&apply_per_sm, tree_apply_kernel<true>,
@@ -686,7 +706,7 @@ cudaError_t launch_meta_stages(const Ctx& c) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&summary_per_sm, tree_summary_kernel<true>, kTreeThreads,
                                                         kTreeSummarySmem);
     if (e != cudaSuccess) return e;
-    apply_per_sm = std::max(1, std::min(apply_per_sm, 4));
+    apply_per_sm = std::max(1, std::min(apply_per_sm, 8));
     summary_per_sm = std::max(1, std::min(summary_per_sm, 4));
   }
   const int tgrid = persistent_blocks(summary_per_sm), agrid = persistent_blocks(apply_per_sm);
