@@ -211,39 +211,54 @@ tree_summary_kernel(const uint8_t* __restrict__ P, const PlanHeader* __restrict_
   }
 }
 
-// exclusive max-scan over tiles, one warp per power value (grid: 1 block of 32 warps); the
-// summaries are stored power-major, so each warp reads consecutive tiles
-__global__ void __launch_bounds__(1024)
+// exclusive max-scan over tiles, one CTA per power value (grid: 32 CTAs of kScanThreads); the
+// summaries are stored power-major, so a CTA reads its power's tiles consecutively: thread k of a
+// chunk takes kScanPer consecutive tiles, the chunk is scanned through the warps' totals, and a
+// running maximum carries from chunk to chunk
+constexpr int kScanThreads = 256, kScanPer = 8;
+__global__ void __launch_bounds__(kScanThreads)
 tree_scan_kernel(const PlanHeader* __restrict__ hdr, const int32_t* __restrict__ summary, int32_t* __restrict__ prefix,
                  int32_t stride) {
-  constexpr int kPer = 16;  // loads in flight per lane
+  __shared__ int32_t s_warp[kScanThreads / 32];
   const int32_t r = hdr->runs;
   const int32_t ntiles = r / kTreeTile + 1;
-  const int lane = threadIdx.x & 31, v = threadIdx.x >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, v = blockIdx.x;
   const int32_t* __restrict__ in = summary + (size_t)v * stride;
   int32_t* __restrict__ out = prefix + (size_t)v * stride;
-  int32_t run = -1;
-  for (int32_t base = 0; base < ntiles; base += 32 * kPer) {
-    int32_t x[kPer];
+  int32_t run = -1;  // maximum over the chunks before this one
+  for (int32_t base = 0; base < ntiles; base += kScanThreads * kScanPer) {
+    const int32_t t0 = base + tid * kScanPer;
+    int32_t x[kScanPer];
+    int32_t mine = -1;
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      const int32_t t = base + q * 32 + lane;
-      x[q] = t < ntiles ? in[t] : -1;
+    for (int q = 0; q < kScanPer; ++q) {
+      x[q] = t0 + q < ntiles ? in[t0 + q] : -1;
+      mine = max(mine, x[q]);
     }
+    int32_t inc = mine;  // inclusive over the warp's threads
 #pragma unroll
-    for (int q = 0; q < kPer; ++q) {
-      int32_t inc = x[q];
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
-        if (lane >= d) inc = max(inc, o);
-      }
-      int32_t exc = __shfl_up_sync(0xffffffffu, inc, 1);
-      if (lane == 0) exc = -1;
-      const int32_t t = base + q * 32 + lane;
-      if (t < ntiles) out[t] = max(run, exc);
-      run = max(run, __shfl_sync(0xffffffffu, inc, 31));
+    for (int d = 1; d < 32; d <<= 1) {
+      const int32_t o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc = max(inc, o);
     }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    int32_t before = __shfl_up_sync(0xffffffffu, inc, 1);  // exclusive over the warp's threads
+    if (lane == 0) before = -1;
+    int32_t chunk = -1;
+#pragma unroll
+    for (int w = 0; w < kScanThreads / 32; ++w) {
+      if (w < warp) before = max(before, s_warp[w]);
+      chunk = max(chunk, s_warp[w]);
+    }
+    before = max(before, run);
+#pragma unroll
+    for (int q = 0; q < kScanPer; ++q) {
+      if (t0 + q < ntiles) out[t0 + q] = before;
+      before = max(before, x[q]);
+    }
+    run = max(run, chunk);
+    __syncthreads();  // s_warp is reused by the next chunk
   }
 }
 
@@ -711,10 +726,10 @@ cudaError_t launch_meta_stages(const Ctx& c) {
   }
   const int tgrid = persistent_blocks(summary_per_sm), agrid = persistent_blocks(apply_per_sm);
   tree_summary_kernel<false><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
-  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
+  tree_scan_kernel<<<32, kScanThreads, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
   tree_apply_kernel<false><<<agrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeL, c.ndepth);
   tree_summary_kernel<true><<<tgrid, kTreeThreads, kTreeSummarySmem, c.stream>>>(c.P, c.hdr, c.tree_sum, c.tree_stride);
-  tree_scan_kernel<<<1, 1024, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
+  tree_scan_kernel<<<32, kScanThreads, 0, c.stream>>>(c.hdr, c.tree_sum, c.tree_pre, c.tree_stride);
   tree_apply_kernel<true><<<agrid, kTreeThreads, kTreeApplySmem, c.stream>>>(c.P, c.hdr, c.tree_pre, c.tree_stride, c.nodeR, c.ndepth);
   plan_kernel<<<grid, 256, 0, c.stream>>>(c.S, c.run_desc, c.P, c.nodeL, c.nodeR, c.ndepth, c.ldepth, c.micro,
                                           c.sub_lim, micro_tile(c.key_bytes), c.small_tasks, c.leaf_items, c.leaf_tile_off,
