@@ -95,6 +95,14 @@ def test_tree_argument_errors_without_gpu(lib):
     assert lib.ps_workspace_size_tree(0, 1, 1000, 0, 1) > lib.ps_workspace_size_tree(0, 1, 1000, 0, 0)
 
 
+def test_bounded_async_argument_errors_without_gpu(lib):
+    ws = ctypes.c_void_p(256)
+    keys = ctypes.c_void_p(4096)
+    # a bound below one element, or one array longer than its bound: rejected before any CUDA call
+    for bound in (0, -5, 9):
+        assert lib.ps_sort_async_bounded_ws(0, keys, None, 10, None, 1, bound, ws, 1 << 20, None) == 1
+
+
 def test_minrun_argument_errors_without_gpu(lib):
     ws = ctypes.c_void_p(256)
     keys = ctypes.c_void_p(4096)
