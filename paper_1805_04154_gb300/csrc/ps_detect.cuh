@@ -71,6 +71,37 @@ __device__ __forceinline__ Fn unpack_thread_fn(uint32_t w) {
   return Fn{w & 63u, (w >> 6) & 63u, (w >> 12) & 63u, (w >> 18) & 63u};
 }
 
+// The same function inside one tile, packed for the block scans: entry state x in bits
+// [16x, 16x + 16) holding the exit state (2 bits) and the run starts produced (14 bits; a tile
+// produces at most kDetectTile of them).  Composing a then b maps entry x to b's entry for a's
+// exit, with a's count added: one extract per entry state, and one 64-bit shuffle per scan step.
+typedef uint64_t TFn;
+__device__ __forceinline__ TFn tfn_identity() { return 0ull | (1ull << 16) | (2ull << 32); }
+__device__ __forceinline__ TFn tfn_of(const Fn& f) {
+  return (uint64_t)((f.map & 3u) | (f.c0 << 2)) | ((uint64_t)(((f.map >> 2) & 3u) | (f.c1 << 2)) << 16) |
+         ((uint64_t)(((f.map >> 4) & 3u) | (f.c2 << 2)) << 32);
+}
+__device__ __forceinline__ Fn fn_of(TFn t) {
+  Fn f;
+  f.map = (uint32_t)(t & 3u) | ((uint32_t)((t >> 16) & 3u) << 2) | ((uint32_t)((t >> 32) & 3u) << 4);
+  f.c0 = (uint32_t)(t & 0xFFFFu) >> 2;
+  f.c1 = (uint32_t)((t >> 16) & 0xFFFFu) >> 2;
+  f.c2 = (uint32_t)((t >> 32) & 0xFFFFu) >> 2;
+  return f;
+}
+__device__ __forceinline__ TFn tfn_then(TFn a, TFn b) {
+  TFn r = 0;
+#pragma unroll
+  for (int x = 0; x < 3; ++x) {
+    const uint32_t ax = (uint32_t)(a >> (16 * x)) & 0xFFFFu;
+    const uint32_t bx = (uint32_t)(b >> (16 * (ax & 3u))) & 0xFFFFu;
+    r |= (uint64_t)(bx + (ax & 0xFFFCu)) << (16 * x);
+  }
+  return r;
+}
+__device__ __forceinline__ uint32_t tfn_exit(TFn t, uint32_t x) { return (uint32_t)(t >> (16 * x)) & 3u; }
+__device__ __forceinline__ uint32_t tfn_cnt(TFn t, uint32_t x) { return ((uint32_t)(t >> (16 * x)) & 0xFFFFu) >> 2; }
+
 // Largest k with offsets[k] <= p (the segment containing p when segments are non-empty).
 __device__ __forceinline__ int32_t segment_of(const int64_t* offsets, int32_t count, int64_t p) {
   int32_t lo = 0, hi = count;  // offsets[0] = 0 <= p
@@ -306,28 +337,29 @@ __global__ void __launch_bounds__(kDetectThreads)
 detect_reduce_kernel(const typename K::T* __restrict__ keys, int64_t n, const int64_t* __restrict__ offsets,
                      int32_t count, uint64_t* __restrict__ tile_agg, uint64_t* __restrict__ thr_L,
                      uint64_t* __restrict__ thr_F, uint32_t* __restrict__ thr_fn) {
-  __shared__ Fn warp_tot[kDetectThreads / 32];
+  __shared__ TFn warp_tot[kDetectThreads / 32];
   __shared__ uint4 stage[kDetectThreads / 32 * 256];  // 4 KB of staged keys per warp
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   ThreadRuns<K> tr;
   tr.load_staged(keys, n, offsets, count, blockIdx.x, tid, stage + warp * 256);
-  Fn incl = tr.aggregate();
+  const Fn mine = tr.aggregate();
   // the emit pass replays the runs from these instead of reading the keys again
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
   thr_L[gt] = tr.L;
   if (offsets != nullptr) thr_F[gt] = tr.F;
-  thr_fn[gt] = pack_thread_fn(incl);
+  thr_fn[gt] = pack_thread_fn(mine);
+  TFn incl = tfn_of(mine);
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const Fn up = fn_shfl_up(incl, d);
-    if (lane >= d) incl = fn_then(up, incl);
+    const TFn up = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl = tfn_then(up, incl);
   }
   if (lane == 31) warp_tot[warp] = incl;
   __syncthreads();
   if (tid == 0) {
-    Fn t = fn_identity();
-    for (int w = 0; w < kDetectThreads / 32; ++w) t = fn_then(t, warp_tot[w]);
-    tile_agg[blockIdx.x] = pack_agg(t);
+    TFn t = tfn_identity();
+    for (int w = 0; w < kDetectThreads / 32; ++w) t = tfn_then(t, warp_tot[w]);
+    tile_agg[blockIdx.x] = pack_agg(fn_of(t));
   }
 }
 
@@ -388,7 +420,7 @@ detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offse
                    const uint64_t* __restrict__ tile_pre, const uint64_t* __restrict__ thr_L,
                    const uint64_t* __restrict__ thr_F, const uint32_t* __restrict__ thr_fn,
                    pos_t* __restrict__ S, uint8_t* __restrict__ run_desc, int32_t* __restrict__ run_seg) {
-  __shared__ Fn warp_tot[kDetectThreads / 32];
+  __shared__ TFn warp_tot[kDetectThreads / 32];
   __shared__ pos_t s_start[kEmitStage];
   __shared__ uint8_t s_desc[kEmitStage];
   __shared__ uint32_t s_count;
@@ -396,26 +428,25 @@ detect_emit_kernel(int64_t n, int64_t run_cap, const int64_t* __restrict__ offse
   const size_t gt = (size_t)blockIdx.x * kDetectThreads + tid;
   ThreadRuns<K> tr;
   tr.restore(n, blockIdx.x, tid, thr_L[gt], offsets != nullptr ? thr_F[gt] : (blockIdx.x == 0 && tid == 0 ? 1ull : 0ull));
-  const Fn agg = unpack_thread_fn(thr_fn[gt]);
-  Fn incl = agg;
+  TFn incl = tfn_of(unpack_thread_fn(thr_fn[gt]));
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    const Fn up = fn_shfl_up(incl, d);
-    if (lane >= d) incl = fn_then(up, incl);
+    const TFn up = __shfl_up_sync(0xffffffffu, incl, d);
+    if (lane >= d) incl = tfn_then(up, incl);
   }
   if (lane == 31) warp_tot[warp] = incl;
-  Fn excl = fn_shfl_up(incl, 1);
-  if (lane == 0) excl = fn_identity();
+  TFn excl = __shfl_up_sync(0xffffffffu, incl, 1);
+  if (lane == 0) excl = tfn_identity();
   __syncthreads();
-  Fn wp = fn_identity();
-  for (int w = 0; w < warp; ++w) wp = fn_then(wp, warp_tot[w]);
-  excl = fn_then(wp, excl);
+  TFn wp = tfn_identity();
+  for (int w = 0; w < warp; ++w) wp = tfn_then(wp, warp_tot[w]);
+  excl = tfn_then(wp, excl);
   const bool staged = offsets == nullptr;  // uniform over the grid
   const uint64_t pre = tile_pre[blockIdx.x];
   const uint32_t tile_entry = (uint32_t)(pre & 3u);
   const uint64_t tile_base = pre >> 2;
-  const uint32_t entry = fn_exit(excl, tile_entry);  // state at position p0 - 1
-  uint64_t idx = tile_base + fn_cnt(excl, tile_entry);
+  const uint32_t entry = tfn_exit(excl, tile_entry);  // state at position p0 - 1
+  uint64_t idx = tile_base + tfn_cnt(excl, tile_entry);
   auto emit = [&](int pos, int32_t seg) {
     const int64_t p = tr.p0 + pos;
     // descending iff the pair (p, p+1) lies inside the segment and is strictly decreasing
